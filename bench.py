@@ -1,0 +1,347 @@
+"""Benchmark: exact k-clique counting on one GB300 through the C ABI.
+
+Workload (one "step" = one pass of the whole path over one graph):
+    Chung-Lu power-law graph, n = 1,000,000, exponent 2.1, mean degree 20,
+    plus 2,000 planted cliques of size U[20, 60] (seed 1), counted for
+    k = 5, 6, 7, 8, 9.  The step runs kc_upload from device buffers
+    (validation, k-core peeling, DAG orientation) and one kc_count per k,
+    then frees the graph.
+Metric: k-cliques/s = (sum of the five counts) / (time per step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The reference arm times the oracle (plain CPU listing, all host cores) on a
+bounded sample of the same workload.  One JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "k-cliques/s (exact count, k=5..9 sweep)"
+UNIT = "k-cliques/s"
+WORKLOAD = "chung_lu_n1e6_g2.1_d20_planted2000x[20,60]_seed1"
+KS = (5, 6, 7, 8, 9)
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--ks", type=str, default=",".join(map(str, KS)))
+    p.add_argument("--small", action="store_true", help="a small graph (for profiling runs)")
+    return p.parse_args()
+
+
+def _graph(small: bool):
+    from paper_2502_00317_gb300 import graphgen as gg
+
+    if small:
+        return gg.chung_lu_planted(n=100_000, n_cliques=200, seed=1), "chung_lu_n1e5_planted200_seed1"
+    return gg.config_chung_lu(), WORKLOAD
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def _max_over_ranks(ws, x: float) -> float:
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(a):
+    import torch
+
+    from paper_2502_00317_gb300 import kclique as kc
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    ks = tuple(int(x) for x in a.ks.split(","))
+    g, workload = _graph(a.small)
+    # inputs resident in HBM before the timed region
+    d_rowptr = torch.from_numpy(g.rowptr.view(np.int64)).cuda()
+    d_col = torch.from_numpy(g.col.view(np.int32)).cuda()
+    # pinned host copies for the end-to-end measurement
+    h_rowptr = torch.from_numpy(g.rowptr.view(np.int64)).pin_memory()
+    h_col = torch.from_numpy(g.col.view(np.int32)).pin_memory()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = kc.Context(local)
+    n = g.n
+
+    def step(host: bool):
+        if host:
+            h = kc.kc_upload(ctx.h, n, h_rowptr, h_col, kc.KC_HOST_PTRS, stream)
+        else:
+            h = kc.kc_upload(ctx.h, n, d_rowptr, d_col, kc.KC_DEVICE_PTRS, stream)
+        up = ctx.upload_stats()
+        counts, stats = [], []
+        for k in ks:
+            counts.append(ctx.count(h, k, stream))
+            stats.append(ctx.stats())
+        ctx.free(h)
+        return counts, up, stats
+
+    for _ in range(a.warmup):
+        counts, _, _ = step(False)
+    units = sum(counts)
+
+    def timed(host: bool):
+        times, ups, sts = [], [], []
+        for _ in range(a.steps):
+            _barrier(ws)
+            flush.fill_(1)  # L2 flush between timed steps (outside the timed interval)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c, up, st = step(host)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            assert sum(c) == units, "count changed between steps"
+            times.append(e0.elapsed_time(e1))
+            ups.append(up)
+            sts.append(st)
+        return times, ups, sts
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    times, ups, sts = timed(False)
+    clocks = sampler.stop()
+    etimes, _, _ = timed(True)
+    ms = _max_over_ranks(ws, statistics.mean(times))
+    ems = _max_over_ranks(ws, statistics.mean(etimes))
+    value = ws * units / (ms / 1e3)
+    evalue = ws * units / (ems / 1e3)
+    launches = sum(u["launches"] + sum(s["total_launches"] for s in st) for u, st in zip(ups, sts))
+    # dominant kernel family: the per-root enumerator (bitmap build + prune + search)
+    enum_ms = statistics.mean(sum(s["ms_enum"] for s in st) for st in sts)
+    enum_launch = statistics.mean(sum(s["enum_launches"] for s in st) for st in sts)
+    build_words = sts[0]
+    bw = sum(s["build_words"] for s in build_words)
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    # algorithmic bytes of the enumerator per step: every DAG word gathered for
+    # the root bitmaps (4 B each) plus the root out-lists (counted in the same
+    # counter) -- see the design doc, roofline section
+    achieved_gbs = (bw * 4) / (enum_ms / 1e3) / 1e9 if enum_ms > 0 else None
+    roof = {
+        "kernel": "k_enum (per-root bitmap build + Alg.5 prune + search/memo), all tiers of one step",
+        "bound": "hbm",
+        "achieved": round(achieved_gbs, 2) if achieved_gbs else None,
+        "peak": hbm,
+        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6800 GB/s",
+        "unit": "GB/s",
+        "frac": round(achieved_gbs / (hbm or 6800.0), 4) if achieved_gbs else None,
+        "traffic": None,
+        "enum_ms_per_step": round(enum_ms, 3),
+        "enum_launches_per_step": enum_launch,
+    }
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32/u64 (exact integer)",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": workload, "ks": list(ks), "counts": counts, "units_per_step": units,
+                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{ws}",
+                   "upload": "device pointers (validate + peel + orient inside the step)"},
+        "e2e": {"value": evalue, "unit": UNIT, "ms_per_step": ems,
+                "h2d_bytes_per_step": int(g.rowptr.nbytes + g.col.nbytes),
+                "d2h_bytes_per_step": 8 * len(ks)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": roof,
+        "stage_ms": {"upload": statistics.mean(u["ms_total"] for u in ups),
+                     "peel": statistics.mean(u["ms_peel"] for u in ups),
+                     "enum_per_k": [round(statistics.mean(st[i]["ms_enum"] for st in sts), 3) for i in range(len(ks))],
+                     "memo_hits_per_k": [sts[0][i]["memo_hits"] for i in range(len(ks))]},
+    }
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(g)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def cpu_baseline(g, ks=(5, 6)):
+    """The oracle on the host cores: full graph, k = 5 and 6 (bounded ~10-30 s)."""
+    import oracle
+
+    t0 = time.time()
+    og = oracle.OracleGraph.from_graph(g)
+    tb = time.time() - t0
+    tot, tt, threads = 0, 0.0, 0
+    for k in ks:
+        t = time.time()
+        c, threads = og.count(k)
+        tt += time.time() - t
+        tot += c
+    return {"value": tot / (tt + tb), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"same graph, k={list(ks)} only (the rest of the k=5..9 sweep takes the oracle ~1 h); "
+                      f"time includes the oracle's own canonicalise+peel+orient ({tb:.1f} s) and counting ({tt:.1f} s)"}
+
+
+# ---------------------------------------------------------- reference arm
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+
+    g, workload = _graph(a.small)
+    ks = (5, 6)
+    times = []
+    units = 0
+    threads = 0
+    for i in range(a.warmup + a.steps):
+        t0 = time.time()
+        og = oracle.OracleGraph.from_graph(g)
+        tot = 0
+        for k in ks:
+            c, threads = og.count(k)
+            tot += c
+        dt = time.time() - t0
+        if i >= a.warmup:
+            times.append(dt)
+        units = tot
+        del og
+    ms = 1e3 * statistics.mean(times)
+    value = units / (ms / 1e3)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32/u64 (exact integer)",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": workload, "ks": list(ks), "units_per_step": units},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "each step: the oracle's canonicalise+peel+orient and counts for k=5,6 on the full graph"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

@@ -1,0 +1,186 @@
+/*
+ * kclique.h -- C ABI of libkc.so: exact k-clique counting and listing on one
+ * GB300 (sm_103a), after DIST (Nam, Jang, Park, Yang, Long; arXiv 2502.00317).
+ *
+ * Problem (Sec. II-A, Definition 1): given a simple undirected graph G and an
+ * integer k, list all k-cliques of G.  A clique is a vertex SET (Sec. II-A),
+ * so a listed clique has no order; this library writes each one as its k
+ * original vertex ids sorted ascending.
+ *
+ * Conventions for every call:
+ *   - every call returns an int status: KC_OK (0) or one of KC_E_*;
+ *     kc_strerror() names it; no C++ exception crosses this boundary;
+ *   - pointers documented "host" are read or written by the CPU, pointers
+ *     documented "device" must be device memory of the context's GPU;
+ *   - `stream` is a cudaStream_t passed as void* (NULL: the context's own
+ *     stream).  Calls that return host results synchronise that stream;
+ *   - a kc_ctx is not thread-safe: one thread at a time per context.
+ */
+#ifndef KCLIQUE_H
+#define KCLIQUE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------- status codes */
+#define KC_OK 0
+#define KC_E_INVALID_ARG 1     /* NULL pointer, k == 0, bad flag, bad range */
+#define KC_E_INVALID_GRAPH 2   /* CSR not simple/symmetric/sorted (without KC_CANONICALIZE) or id >= n */
+#define KC_E_OOM 3             /* a device or host allocation failed */
+#define KC_E_CAPACITY 4        /* listing: more cliques than the output buffer holds */
+#define KC_E_DEVICE_TIMEOUT 5  /* a bounded device-side wait ran out (the context stays usable) */
+#define KC_E_CUDA 6            /* a CUDA runtime call failed */
+#define KC_E_BUSY 7            /* the resource is in use */
+#define KC_E_UNSUPPORTED 8     /* outside the compiled limits (k > KC_MAX_K, out-degree > KC_MAX_OUTDEG) */
+#define KC_E_NOT_FOUND 9       /* unknown graph handle or ticket */
+
+#define KC_MAX_K 64            /* largest k the device enumerator accepts */
+#define KC_MAX_OUTDEG 1024     /* largest out-degree in the degeneracy DAG (bounded by the degeneracy) */
+
+/* ----------------------------------------------------------- upload flags */
+#define KC_HOST_PTRS 0x1u      /* rowptr/col are host pointers (copied to the device) */
+#define KC_DEVICE_PTRS 0x2u    /* rowptr/col are device pointers (copied device-to-device) */
+#define KC_CANONICALIZE 0x4u   /* drop self-loops and repeats, add missing reverse entries, sort rows */
+
+typedef struct kc_ctx kc_ctx;
+typedef uint32_t kc_graph; /* handle of a graph resident on the device, 0 is never valid */
+
+/* Options of a context.  Zero-initialise, set struct_size = sizeof(kc_opts),
+ * then change what you need; a zero field takes its default. */
+typedef struct kc_opts {
+  uint32_t struct_size;
+  uint32_t no_memo;        /* 1: never use the device form of the Induced Subgraph Trie (Sec. IV) */
+  uint32_t no_prune;       /* 1: never prune by soft embeddings (Sec. V, Algorithm 5) */
+  uint32_t split_threshold;/* roots whose estimated work exceeds this many units are split over warps (0: default) */
+  uint64_t memo_bytes;     /* device bytes for the memo tables (0: default 1 GiB); the tau of Sec. VI */
+  uint64_t spin_limit;     /* iterations before a device-side wait gives up (0: default) */
+} kc_opts;
+
+/* Graph facts after upload. */
+typedef struct kc_graph_info {
+  uint32_t n;              /* vertices */
+  uint32_t degeneracy;     /* delta(G): the largest core number (Sec. II-A) */
+  uint64_t m;              /* undirected edges after canonicalisation */
+  uint32_t max_out_degree; /* of the degeneracy DAG; <= degeneracy */
+  uint32_t peel_rounds;    /* parallel peeling rounds used */
+} kc_graph_info;
+
+/* Telemetry of the last kc_count / kc_list call on a context (device times
+ * from CUDA events on the launching stream; counters from the kernels). */
+typedef struct kc_stats {
+  float ms_bin;            /* root filter and binning (a4) */
+  float ms_enum;           /* build + prune + enumerate/memo kernels (a5-a10) */
+  float ms_total;          /* whole call */
+  uint32_t enum_launches;  /* enumerator kernel launches in the call */
+  uint32_t total_launches; /* every kernel launch in the call */
+  uint64_t roots_total;    /* roots with out-degree >= k-1 */
+  uint64_t roots_pruned;   /* of those, dropped by the soft-embedding test on the root */
+  uint64_t roots_heavy;    /* roots handled by the split (heavy) path */
+  uint64_t build_words;    /* 32-bit words read from the DAG while building root bitmaps */
+  uint64_t memo_hits;      /* device trie hits */
+  uint64_t memo_inserts;   /* device trie insertions */
+  uint64_t memo_full;      /* insertions refused because a table was full */
+} kc_stats;
+
+/* Per-stage device times of the last kc_upload (CUDA events). */
+typedef struct kc_upload_stats {
+  float ms_copy;           /* H2D or D2D copy of the CSR */
+  float ms_canon;          /* validation or canonicalisation (a1) */
+  float ms_peel;           /* k-core peeling (a2) */
+  float ms_orient;         /* DAG orientation and relabelling (a3) */
+  float ms_total;
+  uint32_t launches;
+} kc_upload_stats;
+
+/* Create a context on CUDA device `device`.  opts may be NULL.  *out receives
+ * the context, which owns every device buffer it allocates. */
+int kc_create(kc_ctx** out, int device, const kc_opts* opts);
+
+/* Destroy a context and every graph still resident in it. */
+int kc_destroy(kc_ctx* ctx);
+
+/*
+ * Upload a graph given as CSR with n vertices (ids 0..n-1): rowptr has n+1
+ * uint64 entries, col has rowptr[n] uint32 entries.  flags must contain
+ * exactly one of KC_HOST_PTRS / KC_DEVICE_PTRS.  The arrays stay owned by the
+ * caller; they are copied.  Without KC_CANONICALIZE the CSR must already be
+ * simple (Sec. II-A): no self-loop, no repeat, every entry's reverse present,
+ * rows sorted ascending, else KC_E_INVALID_GRAPH.  With KC_CANONICALIZE any
+ * entries with ids < n are accepted and cleaned on the device.
+ *
+ * The upload then computes on the device, with no host round trip per round:
+ *   - the degeneracy order (Sec. II-A) by parallel k-core peeling, order key
+ *     (core number, peeling round, id);
+ *   - the DAG based on it (Sec. II-A), relabelled to rank space, each out-list
+ *     sorted ascending (Algorithm 2, first line).
+ * *out receives the handle.  Synchronises the stream.
+ */
+int kc_upload(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr, const uint32_t* col, uint32_t flags,
+              kc_graph* out, void* stream);
+
+/* Release a graph's device memory. */
+int kc_free_graph(kc_ctx* ctx, kc_graph g);
+
+/* Facts about an uploaded graph (host struct). */
+int kc_graph_info_get(kc_ctx* ctx, kc_graph g, kc_graph_info* info);
+
+/*
+ * Copy the upload's results to caller-owned host arrays (any may be NULL):
+ * core[n] core numbers, rank[n] position of each vertex in the order,
+ * orow[n+1] and ocol[m] the DAG in rank space (out-list of rank r is
+ * ocol[orow[r] .. orow[r+1]), ranks ascending).  For tests and tooling.
+ */
+int kc_export_dag(kc_ctx* ctx, kc_graph g, uint32_t* core, uint32_t* rank, uint64_t* orow, uint32_t* ocol);
+
+/*
+ * Count the k-cliques of an uploaded graph (Definition 1) into *count (host).
+ * k = 1 gives n, k = 2 gives m.  Work per root u of the DAG: the (k-1)-cliques
+ * of the subgraph induced by N(u) (Algorithm 2), pruned by soft embeddings
+ * (Sec. V) and, for dense subgraphs by Eq. (1), reusing repeated sub-counts
+ * through a device form of the Induced Subgraph Trie (Sec. IV, Algorithms
+ * 3-4).  Synchronises the stream.
+ */
+int kc_count(kc_ctx* ctx, kc_graph g, uint32_t k, uint64_t* count, void* stream);
+
+/*
+ * List every k-clique into d_buf (device, caller-owned, room for cap tuples
+ * of k uint32 ids): tuple i occupies d_buf[i*k .. i*k+k-1], ids ascending;
+ * the order of tuples is unspecified.  *written (host) = tuples written =
+ * min(total, cap); *total = all k-cliques; *checksum = sum mod 2^64 over all
+ * k-cliques of the SplitMix64-chained hash of its sorted id tuple (h =
+ * mix(0x9E3779B97F4A7C15 ^ k), then h = mix(h ^ id) for each id ascending).
+ * total and checksum always cover every clique; when total > cap the call
+ * still fills d_buf with an unspecified subset and returns KC_E_CAPACITY.
+ * cap may be 0 (d_buf may then be NULL) to get total and checksum only.
+ * Synchronises the stream.
+ */
+int kc_list(kc_ctx* ctx, kc_graph g, uint32_t k, uint32_t* d_buf, uint64_t cap, uint64_t* written,
+            uint64_t* total, uint64_t* checksum, void* stream);
+
+/*
+ * As kc_list, restricted to the k-cliques whose first vertex in the
+ * degeneracy order has rank in [root_lo, root_hi) (one NodeParallel subtask
+ * per root, Sec. VII-D).  Disjoint ranges partition the cliques, so their
+ * totals add and their checksums wrap-add to the full listing's.
+ */
+int kc_list_range(kc_ctx* ctx, kc_graph g, uint32_t k, uint32_t root_lo, uint32_t root_hi, uint32_t* d_buf,
+                  uint64_t cap, uint64_t* written, uint64_t* total, uint64_t* checksum, void* stream);
+
+/* Telemetry of the last count/list call, and of the last upload. */
+int kc_last_stats(kc_ctx* ctx, kc_stats* out);
+int kc_last_upload_stats(kc_ctx* ctx, kc_upload_stats* out);
+
+/* Name of a status code (static string). */
+const char* kc_strerror(int status);
+
+/* Text of the last CUDA error seen by the context (static per context). */
+const char* kc_last_error(kc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KCLIQUE_H */

@@ -1,0 +1,890 @@
+// kc_enum.cu -- per-root enumeration of libkc.so (one warp per root of the DAG).
+//
+// For a root u with d out-neighbours the warp
+//   1. builds the DAG induced by N(u) (Algorithm 2: the subgraph G_u) as a
+//      d x d bit-matrix in root-local indices 0..d-1 (out-neighbours sorted by
+//      rank, so row i holds only columns j > i);
+//   2. runs Algorithm 5 on G[N(u) ∪ {u}] (Sec. V): r_i for every local vertex
+//      and r(u) for the root, capped at k; the root is dropped when r(u) < k
+//      (Lemma 1).  Below the root the same r_i bound a pick: vertex v can be
+//      the minimum of an l-clique inside any subgraph of G_u only if r_v >= l;
+//   3. lists or counts the (k-1)-cliques of G_u by depth-first search over
+//      candidate bitmaps (Algorithm 1/2 recursion, intersections are AND of
+//      bitmap rows, sizes are popcounts):
+//        - count mode stops two levels early: the 2-cliques of a candidate set
+//          S are the edges sum_{v in S} popc(S & row(v));
+//        - list mode emits each clique at the last level;
+//        - the memo variant (count mode) is the device form of the Induced
+//          Subgraph Trie (Sec. IV, Algorithms 3 and 4): f(S, l), the number of
+//          l-cliques in G[S], is stored in a per-warp hash table keyed by
+//          (S, l).  A frame walks S from its largest vertex down (the order of
+//          the identifying string) and after each vertex v stores the count
+//          of the prefix subgraph S ∩ [v, ∞) -- the trie path node t_i with
+//          Marked[l] set.  A frame starts from its longest stored prefix
+//          (binary search over the prefix lengths), and an (S, l) that is
+//          stored whole is a retrieval (ListingIST) instead of a search.  The
+//          Eq. (1) density test decides where this starts; below a dense
+//          frame every frame is memoised, as Algorithm 3 recurses into itself.
+#include <algorithm>
+
+#include "kc_internal.cuh"
+
+namespace kc {
+
+constexpr int KMAX = KC_MAX_K;  // stack depth bound (k - 1 <= KMAX - 1)
+
+struct EnumKArgs {
+  const uint64_t* orow;
+  const uint32_t* ocol;
+  const uint32_t* vert;
+  const uint32_t* roots;
+  uint32_t nroots;
+  unsigned int* qctr;
+  uint32_t k;
+  int prune;
+  int memo;
+  uint32_t* out;
+  unsigned long long cap;
+  unsigned long long* acc;
+  uint8_t* gstate;            // per-warp state in global memory (heavy tiers)
+  unsigned long long gstride; // bytes per warp
+  uint32_t* memo_tags;        // per-warp tables: cap entries each
+  uint32_t* memo_keys;
+  unsigned long long* memo_vals;
+  uint32_t memo_cap;          // entries per warp (power of two)
+  uint32_t* status;
+};
+
+// Per-warp working state, carved from shared or global memory.
+template <int W>
+struct WarpState {
+  uint32_t* nbr;              // [32W] ranks of N+(u), ascending
+  uint32_t* rows;             // [32W*W] bit-matrix rows
+  uint32_t* masks;            // [KMAX*W] masks[l*W+w]: local vertices with r >= l
+  uint32_t* cand;             // [KMAX*W] candidate set per depth
+  unsigned long long* sum;    // [KMAX] frame partial counts (memo variant)
+  int32_t* pos;               // [KMAX] next pick position (descending), -1 when done
+  int32_t* cur;               // [KMAX] vertex whose child frame is open
+  uint32_t* sid;              // [KMAX+1] sorted original ids of the open clique prefix
+  uint8_t* sins;              // [KMAX] insertion index of each pick in sid
+  uint8_t* rr;                // [32W] r values (Algorithm 5), capped at k
+  uint8_t* dense;             // [KMAX] frame uses the memo
+  uint8_t* fullins;           // [KMAX] frame's whole set already stored
+  __host__ __device__ static constexpr size_t bytes() {
+    return (size_t)32 * W * 4 + (size_t)32 * W * W * 4 + (size_t)KMAX * W * 4 * 2 + (size_t)KMAX * 8 +
+           (size_t)KMAX * 4 * 2 + (size_t)(KMAX + 1) * 4 + KMAX + 32 * W + KMAX * 2 + 16;
+  }
+  __device__ void carve(uint8_t* base) {
+    uint8_t* p = base;
+    sum = (unsigned long long*)p; p += (size_t)KMAX * 8;
+    nbr = (uint32_t*)p; p += (size_t)32 * W * 4;
+    rows = (uint32_t*)p; p += (size_t)32 * W * W * 4;
+    masks = (uint32_t*)p; p += (size_t)KMAX * W * 4;
+    cand = (uint32_t*)p; p += (size_t)KMAX * W * 4;
+    pos = (int32_t*)p; p += (size_t)KMAX * 4;
+    cur = (int32_t*)p; p += (size_t)KMAX * 4;
+    sid = (uint32_t*)p; p += (size_t)(KMAX + 1) * 4;
+    sins = p; p += KMAX;
+    rr = p; p += 32 * W;
+    dense = p; p += KMAX;
+    fullins = p;
+  }
+};
+
+template <int W>
+__host__ __device__ constexpr size_t warp_state_bytes() {
+  return (WarpState<W>::bytes() + 15) & ~(size_t)15;
+}
+
+// ------------------------------------------------------------ bit helpers
+// Largest set bit of (S & M) at index <= from, or -1.
+template <int W>
+__device__ __forceinline__ int next_desc(const uint32_t* S, const uint32_t* M, int from) {
+  if (from < 0) return -1;
+  int w = from >> 5;
+  uint32_t x = S[w] & M[w] & (0xFFFFFFFFu >> (31 - (from & 31)));
+  while (true) {
+    if (x) return (w << 5) + 31 - __clz(x);
+    if (--w < 0) return -1;
+    x = S[w] & M[w];
+  }
+}
+
+template <int W>
+__device__ __forceinline__ int top_bit(const uint32_t (&c)[W]) {
+#pragma unroll
+  for (int w = W - 1; w >= 0; w--)
+    if (c[w]) return (w << 5) + 31 - __clz(c[w]);
+  return -1;
+}
+
+// c[i] without a dynamic register-array index.
+template <int W>
+__device__ __forceinline__ uint32_t word_at(const uint32_t (&c)[W], uint32_t i) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int w = 0; w < W; w++) r = ((uint32_t)w == i) ? c[w] : r;
+  return r;
+}
+
+// Number of edges of G[S] (the 2-cliques of S); lane-partial.
+template <int W>
+__device__ __forceinline__ uint32_t edges_partial(const uint32_t (&S)[W], const uint32_t* rows) {
+  const uint32_t lane = lane_id();
+  uint32_t c = 0;
+#pragma unroll
+  for (int w = 0; w < W; w++) {
+    if ((S[w] >> lane) & 1u) {
+      const uint32_t* rv = rows + (size_t)((w << 5) + lane) * W;
+#pragma unroll
+      for (int w2 = w; w2 < W; w2++) c += __popc(S[w2] & rv[w2]);
+    }
+  }
+  return c;
+}
+
+// ------------------------------------------------------------------- memo
+struct Memo {
+  uint32_t* tags;
+  uint32_t* keys;
+  unsigned long long* vals;
+  uint32_t cap;
+  uint32_t tagbase;  // epoch << 7
+};
+
+template <int W>
+__device__ __forceinline__ uint32_t memo_hash(const uint32_t (&key)[W], uint32_t l) {
+  uint32_t h = 0x9E3779B9u * (l + 1u);
+#pragma unroll
+  for (int w = 0; w < W; w++) {
+    h ^= key[w] + 0x7F4A7C15u + (h << 6) + (h >> 2);
+    h *= 0x85EBCA6Bu;
+  }
+  h ^= h >> 15;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 13;
+  return h;
+}
+
+// Warp-wide probe of a 32-slot window; returns the matching slot or -1, and
+// (by reference) the first free slot of the window or -1.
+template <int W>
+__device__ __forceinline__ int memo_probe(const Memo& m, const uint32_t (&key)[W], uint32_t l, int* free_slot) {
+  const uint32_t lane = lane_id();
+  uint32_t h = memo_hash<W>(key, l);
+  uint32_t slot = (h + lane) & (m.cap - 1);
+  uint32_t t = m.tags[slot];
+  uint32_t want = m.tagbase | l;
+  bool match = false;
+  if (t == want) {
+    match = true;
+#pragma unroll
+    for (int w = 0; w < W; w++) match &= (m.keys[(size_t)slot * W + w] == key[w]);
+  }
+  uint32_t bm = __ballot_sync(0xFFFFFFFFu, match);
+  uint32_t be = __ballot_sync(0xFFFFFFFFu, (t & ~0x7Fu) != m.tagbase);
+  *free_slot = be ? (int)((h + __ffs(be) - 1) & (m.cap - 1)) : -1;
+  return bm ? (int)((h + __ffs(bm) - 1) & (m.cap - 1)) : -1;
+}
+
+template <int W>
+__device__ __forceinline__ bool memo_find(const Memo& m, const uint32_t (&key)[W], uint32_t l,
+                                          unsigned long long* val) {
+  int fs;
+  int s = memo_probe<W>(m, key, l, &fs);
+  if (s < 0) return false;
+  *val = m.vals[s];
+  return true;
+}
+
+// Store (key, l) -> val; returns 1 if stored, 0 if the window was full.
+template <int W>
+__device__ __forceinline__ int memo_store(const Memo& m, const uint32_t (&key)[W], uint32_t l, unsigned long long val) {
+  int fs;
+  int s = memo_probe<W>(m, key, l, &fs);
+  if (s < 0) s = fs;
+  if (s < 0) return 0;
+  const uint32_t lane = lane_id();
+  if (lane < W) m.keys[(size_t)s * W + lane] = word_at<W>(key, lane);
+  if (lane == 0) {
+    m.vals[s] = val;
+    m.tags[s] = m.tagbase | l;
+  }
+  __syncwarp();
+  return 1;
+}
+
+// Bits of c at index >= v.
+template <int W>
+__device__ __forceinline__ void suffix_of(const uint32_t (&c)[W], int v, uint32_t (&out)[W]) {
+#pragma unroll
+  for (int w = 0; w < W; w++) {
+    int lo = w << 5;
+    out[w] = (v <= lo) ? c[w] : (v >= lo + 32 ? 0u : (c[w] & (0xFFFFFFFFu << (v - lo))));
+  }
+}
+
+// Position of the j-th set bit (0-based, ascending) of c.
+template <int W>
+__device__ __forceinline__ int select_bit(const uint32_t (&c)[W], int j) {
+#pragma unroll
+  for (int w = 0; w < W; w++) {
+    int p = __popc(c[w]);
+    if (j < p) {
+      uint32_t x = c[w];
+      for (int i = 0; i < j; i++) x &= x - 1;
+      return (w << 5) + __ffs(x) - 1;
+    }
+    j -= p;
+  }
+  return -1;
+}
+
+// ----------------------------------------------------------- the kernel
+// MODE 0: count (plain), 1: list, 2: count with memo.
+template <int W, int MODE>
+__global__ void __launch_bounds__(256) k_enum(EnumKArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t lane = lane_id();
+  const uint32_t wib = threadIdx.x >> 5;
+  const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  WarpState<W> st;
+  if (a.gstate) st.carve(a.gstate + gwarp * a.gstride);
+  else st.carve(smem + (size_t)wib * warp_state_bytes<W>());
+
+  const uint32_t k = a.k;
+  const uint32_t need = k - 1;  // vertices to pick inside G_u
+  unsigned long long acc_cnt = 0, acc_sum = 0;
+  unsigned long long st_pruned = 0, st_words = 0, st_hits = 0, st_ins = 0, st_full = 0;
+  Memo memo{};
+  uint32_t epoch = 0;
+  if (MODE == 2) {
+    memo.tags = a.memo_tags + gwarp * a.memo_cap;
+    memo.keys = a.memo_keys + gwarp * a.memo_cap * W;
+    memo.vals = a.memo_vals + gwarp * a.memo_cap;
+    memo.cap = a.memo_cap;
+  }
+
+  while (true) {
+    uint32_t qi = 0;
+    if (lane == 0) qi = atomicAdd(a.qctr, 1u);
+    qi = __shfl_sync(0xFFFFFFFFu, qi, 0);
+    if (qi >= a.nroots) break;
+    const uint32_t u = a.roots[qi];
+    const uint64_t ob = a.orow[u];
+    const int d = (int)(a.orow[u + 1] - ob);
+
+    // ---- 1. bit-matrix of G_u
+    for (int i = lane; i < d; i += 32) st.nbr[i] = a.ocol[ob + i];
+    for (int i = lane; i < d * W; i += 32) st.rows[i] = 0u;
+    __syncwarp();
+    const uint32_t last = st.nbr[d - 1];
+    uint32_t words = 0;
+    for (int i = 0; i < d - 1; i++) {
+      const uint32_t v = st.nbr[i];
+      const uint64_t b = a.orow[v], e = a.orow[v + 1];
+      for (uint64_t p0 = b; p0 < e; p0 += 32) {
+        uint64_t p = p0 + lane;
+        uint32_t w = p < e ? a.ocol[p] : 0xFFFFFFFFu;
+        words += (p < e);
+        if (w <= last) {
+          int lo = i + 1, hi = d;  // search nbr[i+1 .. d)
+          while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (st.nbr[mid] < w) lo = mid + 1;
+            else hi = mid;
+          }
+          if (lo < d && st.nbr[lo] == w) atomicOr(&st.rows[(size_t)i * W + (lo >> 5)], 1u << (lo & 31));
+        }
+        if (__all_sync(0xFFFFFFFFu, w > last)) break;
+      }
+    }
+    st_words += words;
+    __syncwarp();
+
+    // ---- 2. Algorithm 5 on G[N(u) ∪ {u}], r capped at k
+    const uint32_t rcap = k;
+    uint32_t root_r = rcap;
+    if (a.prune) {
+      if (lane == 0) {
+        for (int i = d - 1; i >= 0; i--) {
+          uint32_t c = 1;
+          const uint32_t* row = st.rows + (size_t)i * W;
+          for (int w = W - 1; w >= 0 && c < rcap; w--) {
+            uint32_t x = row[w];
+            while (x && c < rcap) {
+              int b = 31 - __clz(x);
+              x &= ~(1u << b);
+              if (c <= st.rr[(w << 5) + b]) c++;
+            }
+          }
+          st.rr[i] = (uint8_t)c;
+        }
+        uint32_t c = 1;
+        for (int j = d - 1; j >= 0 && c < rcap; j--)
+          if (c <= st.rr[j]) c++;
+        root_r = c;
+      }
+      root_r = __shfl_sync(0xFFFFFFFFu, root_r, 0);
+      __syncwarp();
+      if (root_r < k) {
+        st_pruned++;
+        continue;
+      }
+    } else {
+      for (int i = lane; i < d; i += 32) st.rr[i] = (uint8_t)rcap;
+      __syncwarp();
+    }
+    // masks[l] = local vertices with r >= l, for l in [1, k-1]
+    for (uint32_t l = 1; l <= need; l++) {
+#pragma unroll
+      for (int w = 0; w < W; w++) {
+        int i = (w << 5) + lane;
+        bool b = i < d && st.rr[i] >= l;
+        uint32_t m = __ballot_sync(0xFFFFFFFFu, b);
+        if (lane == 0) st.masks[l * W + w] = m;
+      }
+    }
+    __syncwarp();
+
+    // ---- 3. search
+    uint32_t S0[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+      int lo = w << 5;
+      S0[w] = d >= lo + 32 ? 0xFFFFFFFFu : (d <= lo ? 0u : (0xFFFFFFFFu >> (lo + 32 - d)));
+    }
+
+    if (MODE == 0 || MODE == 1) {
+      // plain depth-first search
+      if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
+      if (lane == 0) {
+        st.pos[0] = d - 1;
+        st.sid[0] = a.vert[u];
+      }
+      __syncwarp();
+      int depth = 0;
+      while (depth >= 0) {
+        const uint32_t l = need - depth;  // vertices still to pick from cand[depth]
+        const uint32_t* S = st.cand + depth * W;
+        if (MODE == 0 && l == 2) {
+          uint32_t s[W];
+#pragma unroll
+          for (int w = 0; w < W; w++) s[w] = S[w];
+          acc_cnt += edges_partial<W>(s, st.rows);
+          depth--;
+          continue;
+        }
+        if (l == 1) {
+          if (MODE == 0) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int w = 0; w < W; w++) c += __popc(S[w]);
+            if (lane == 0) acc_cnt += c;
+          } else {
+            // emit C ∪ {x} for each x in S: ids sorted, hashed, written
+            const int plen = depth + 1;  // root + picks
+#pragma unroll 1
+            for (int w = 0; w < W; w++) {
+              uint32_t x = S[w];
+              if (!x) continue;
+              bool mine = (x >> lane) & 1u;
+              unsigned long long base = 0;
+              if (lane == 0) base = atomicAdd(&a.acc[kAccWritten], (unsigned long long)__popc(x));
+              base = __shfl_sync(0xFFFFFFFFu, base, 0);
+              if (mine) {
+                uint32_t id = a.vert[st.nbr[(w << 5) + lane]];
+                unsigned long long slot = base + __popc(x & lanemask_lt());
+                bool wr = slot < a.cap;
+                uint32_t* o = a.out + slot * (unsigned long long)k;
+                uint64_t h = mix64(0x9E3779B97F4A7C15ull ^ (uint64_t)k);
+                int j = 0;
+                bool placed = false;
+                for (int q = 0; q < plen; q++) {
+                  uint32_t y = st.sid[q];
+                  if (!placed && id < y) {
+                    h = mix64(h ^ (uint64_t)id);
+                    if (wr) o[j] = id;
+                    j++;
+                    placed = true;
+                  }
+                  h = mix64(h ^ (uint64_t)y);
+                  if (wr) o[j] = y;
+                  j++;
+                }
+                if (!placed) {
+                  h = mix64(h ^ (uint64_t)id);
+                  if (wr) o[j] = id;
+                }
+                acc_sum += h;
+                acc_cnt += 1;
+              }
+            }
+          }
+          depth--;
+          if (MODE == 1 && depth >= 0) {
+            // remove the pick of `depth` from the sorted prefix
+            __syncwarp();
+            if (lane == 0) {
+              int plen = depth + 2;
+              for (int q = st.sins[depth]; q + 1 < plen; q++) st.sid[q] = st.sid[q + 1];
+            }
+            __syncwarp();
+          }
+          continue;
+        }
+        int v = next_desc<W>(S, st.masks + l * W, st.pos[depth]);
+        if (v < 0) {
+          depth--;
+          if (MODE == 1 && depth >= 0) {
+            __syncwarp();
+            if (lane == 0) {
+              int plen = depth + 2;
+              for (int q = st.sins[depth]; q + 1 < plen; q++) st.sid[q] = st.sid[q + 1];
+            }
+            __syncwarp();
+          }
+          continue;
+        }
+        uint32_t c[W];
+        uint32_t sz = 0, anym = 0;
+        const uint32_t* rv = st.rows + (size_t)v * W;
+        const uint32_t* mk = st.masks + (l - 1) * W;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+          c[w] = S[w] & rv[w];
+          sz += __popc(c[w]);
+          anym |= c[w] & mk[w];
+        }
+        __syncwarp();
+        if (lane == 0) st.pos[depth] = v - 1;
+        if (sz >= l - 1 && anym) {
+          if (lane < W) st.cand[(depth + 1) * W + lane] = word_at<W>(c, lane);
+          if (lane == 0) {
+            st.pos[depth + 1] = top_bit<W>(c);
+            if (MODE == 1) {
+              // insert the pick's id into the sorted prefix
+              uint32_t id = a.vert[st.nbr[v]];
+              int plen = depth + 1;
+              int q = plen;
+              while (q > 0 && st.sid[q - 1] > id) {
+                st.sid[q] = st.sid[q - 1];
+                q--;
+              }
+              st.sid[q] = id;
+              st.sins[depth] = (uint8_t)q;
+            }
+          }
+          depth++;
+        }
+        __syncwarp();
+      }
+    } else {
+      // ---- memoised count (device form of the Induced Subgraph Trie)
+      if (++epoch >= (1u << 25)) {
+        for (uint32_t i = lane; i < memo.cap; i += 32) memo.tags[i] = 0u;
+        __syncwarp();
+        epoch = 1;
+      }
+      memo.tagbase = epoch << 7;
+      // root frame density, Eq. (1): 2 l |E| > (l - 1) |V|^2 with l = k - 1
+      uint32_t er = 0;
+      for (int i = lane; i < d * W; i += 32) er += __popc(st.rows[i]);
+      er = warp_sum(er);
+      const uint32_t l0 = need;
+      bool dense0 = a.memo && l0 > 3 && 2ull * l0 * er > (unsigned long long)(l0 - 1) * d * d;
+      if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
+      if (lane == 0) {
+        st.pos[0] = d - 1;
+        st.sum[0] = 0;
+        st.dense[0] = dense0;
+        st.fullins[0] = 0;
+      }
+      __syncwarp();
+      int depth = 0;
+      unsigned long long root_total = 0;
+      while (true) {
+        const uint32_t l = need - depth;
+        uint32_t S[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) S[w] = st.cand[depth * W + w];
+        const bool fd = st.dense[depth];
+        int v = next_desc<W>(st.cand + depth * W, st.masks + l * W, st.pos[depth]);
+        if (v < 0) {
+          unsigned long long val = st.sum[depth];
+          if (fd && !st.fullins[depth]) {
+            int okk = memo_store<W>(memo, S, l, val);
+            st_ins += okk;
+            st_full += 1 - okk;
+          }
+          if (depth == 0) {
+            root_total = val;
+            break;
+          }
+          depth--;
+          const uint32_t lp = need - depth;
+          uint32_t P[W];
+#pragma unroll
+          for (int w = 0; w < W; w++) P[w] = st.cand[depth * W + w];
+          unsigned long long ps = st.sum[depth] + val;
+          const int pv = st.cur[depth];
+          __syncwarp();
+          if (lane == 0) st.sum[depth] = ps;
+          if (st.dense[depth]) {
+            uint32_t T[W];
+            suffix_of<W>(P, pv, T);
+            int okk = memo_store<W>(memo, T, lp, ps);
+            st_ins += okk;
+            st_full += 1 - okk;
+            // whole set stored when pv is the smallest vertex of P
+            bool whole = true;
+#pragma unroll
+            for (int w = 0; w < W; w++) whole &= (T[w] == P[w]);
+            if (lane == 0 && whole) st.fullins[depth] = 1;
+          }
+          __syncwarp();
+          continue;
+        }
+        __syncwarp();
+        if (lane == 0) st.pos[depth] = v - 1;
+        uint32_t c[W];
+        uint32_t sz = 0;
+        const uint32_t* rv = st.rows + (size_t)v * W;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+          c[w] = S[w] & rv[w];
+          sz += __popc(c[w]);
+        }
+        const uint32_t cl = l - 1;
+        unsigned long long val = 0;
+        bool resolved = true;
+        bool cd = false;
+        unsigned long long start_sum = 0;
+        int start_pos = -1;
+        if (cl == 1) {
+          val = sz;
+        } else if (cl == 2) {
+          val = warp_sum(edges_partial<W>(c, st.rows));
+        } else {
+          uint32_t anym = 0;
+          const uint32_t* mk = st.masks + cl * W;
+#pragma unroll
+          for (int w = 0; w < W; w++) anym |= c[w] & mk[w];
+          if (sz >= cl && anym) {
+            cd = fd;
+            if (!cd && a.memo && cl > 3) {
+              uint32_t e = warp_sum(edges_partial<W>(c, st.rows));
+              cd = 2ull * cl * e > (unsigned long long)(cl - 1) * sz * sz;
+            }
+            if (cd && memo_find<W>(memo, c, cl, &val)) {
+              st_hits++;
+            } else {
+              resolved = false;
+              start_pos = top_bit<W>(c);
+              if (cd) {
+                // longest stored prefix (largest-vertex side) of c at level cl:
+                // the smallest j in [1, m] whose suffix c ∩ [p_j, ∞) is stored
+                // (j = m stands for the empty suffix, count 0).
+                int m = 0;
+#pragma unroll
+                for (int w = 0; w < W; w++) m += __popc(c[w]);
+                int lo = 1, hi = m;
+                unsigned long long hv = 0;
+                while (lo < hi) {
+                  int mid = (lo + hi) >> 1;
+                  uint32_t T[W];
+                  suffix_of<W>(c, select_bit<W>(c, mid), T);
+                  unsigned long long tv;
+                  if (memo_find<W>(memo, T, cl, &tv)) {
+                    hi = mid;
+                    hv = tv;
+                  } else {
+                    lo = mid + 1;
+                  }
+                }
+                if (hi < m) {
+                  start_sum = hv;
+                  start_pos = select_bit<W>(c, hi) - 1;
+                  st_hits++;
+                }
+              }
+            }
+          }
+        }
+        if (resolved) {
+          unsigned long long ns = st.sum[depth] + val;
+          __syncwarp();
+          if (lane == 0) st.sum[depth] = ns;
+          if (fd) {
+            uint32_t T[W];
+            suffix_of<W>(S, v, T);
+            int okk = memo_store<W>(memo, T, l, ns);
+            st_ins += okk;
+            st_full += 1 - okk;
+            bool whole = true;
+#pragma unroll
+            for (int w = 0; w < W; w++) whole &= (T[w] == S[w]);
+            if (lane == 0 && whole) st.fullins[depth] = 1;
+          }
+          __syncwarp();
+          continue;
+        }
+        // open the child frame
+        if (lane < W) st.cand[(depth + 1) * W + lane] = word_at<W>(c, lane);
+        if (lane == 0) {
+          st.cur[depth] = v;
+          st.pos[depth + 1] = start_pos;
+          st.sum[depth + 1] = start_sum;
+          st.dense[depth + 1] = cd;
+          st.fullins[depth + 1] = 0;
+        }
+        __syncwarp();
+        depth++;
+      }
+      if (lane == 0) acc_cnt += root_total;
+    }
+    __syncwarp();
+  }
+  // ---- reduce this warp's partials
+  acc_cnt = warp_sum(acc_cnt);
+  acc_sum = warp_sum(acc_sum);
+  st_words = warp_sum(st_words);
+  if (lane == 0) {
+    if (acc_cnt) atomicAdd(&a.acc[kAccCount], acc_cnt);
+    if (acc_sum) atomicAdd(&a.acc[kAccChecksum], acc_sum);
+    if (st_pruned) atomicAdd(&a.acc[kAccRootsPruned], st_pruned);
+    if (st_words) atomicAdd(&a.acc[kAccBuildWords], st_words);
+    if (st_hits) atomicAdd(&a.acc[kAccMemoHits], st_hits);
+    if (st_ins) atomicAdd(&a.acc[kAccMemoInserts], st_ins);
+    if (st_full) atomicAdd(&a.acc[kAccMemoFull], st_full);
+  }
+}
+
+// k = 1 listing: every vertex of the rank range is a clique.
+__global__ void k_list_singletons(const uint32_t* __restrict__ vert, uint32_t lo, uint32_t hi,
+                                  uint32_t* __restrict__ out, unsigned long long cap, unsigned long long* acc) {
+  unsigned long long s = 0, c = 0;
+  for (uint64_t r = (uint64_t)lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < hi;
+       r += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t id = vert[r];
+    unsigned long long slot = r - lo;
+    if (slot < cap) out[slot] = id;
+    s += mix64(mix64(0x9E3779B97F4A7C15ull ^ 1ull) ^ (uint64_t)id);
+    c++;
+  }
+  s = warp_sum(s);
+  c = warp_sum(c);
+  if (lane_id() == 0 && c) {
+    atomicAdd(&acc[kAccChecksum], s);
+    atomicAdd(&acc[kAccCount], c);
+    atomicAdd(&acc[kAccWritten], c);
+  }
+}
+
+// Roots of [lo, hi) with out-degree >= k-1, binned by bitmap width.
+__host__ __device__ constexpr int tier_words(int t) { return 1 << t; }  // 1, 2, 4, ..., 32 words
+
+__global__ void k_bin_roots(const uint64_t* __restrict__ orow, uint32_t lo, uint32_t hi, uint32_t need,
+                            uint32_t* __restrict__ lists, uint32_t list_cap, uint32_t* __restrict__ cnts,
+                            unsigned long long* acc) {
+  unsigned long long tot = 0;
+  for (uint64_t r = (uint64_t)lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < hi;
+       r += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t d = (uint32_t)(orow[r + 1] - orow[r]);
+    if (d < need || d == 0) continue;
+    tot++;
+    uint32_t words = (d + 31) >> 5;
+    int t = 0;
+    while (t < kTiers && tier_words(t) < (int)words) t++;
+    if (t < kTiers) {
+      uint32_t p = atomicAdd(&cnts[t], 1u);
+      lists[(size_t)t * list_cap + p] = (uint32_t)r;
+    } else {
+      atomicAdd(&cnts[kTiers], 1u);
+    }
+  }
+  tot = warp_sum(tot);
+  if (lane_id() == 0 && tot) atomicAdd(&acc[kAccRootsTotal], tot);
+}
+
+// --------------------------------------------------------------- launcher
+struct TierPlan {
+  int W = 0;
+  int mode = 0;
+  uint32_t nroots = 0;
+  int warps_per_block = 0;
+  size_t smem = 0;
+  uint64_t blocks = 0;
+  uint64_t gstate_bytes = 0;   // per-warp state in global memory (0: in shared memory)
+  uint32_t memo_cap = 0;       // entries per warp (0: no memo)
+  uint64_t memo_bytes = 0;
+  const void* fn = nullptr;
+};
+
+template <int W, int MODE>
+static int plan_tier(kc_ctx* ctx, uint32_t nroots, TierPlan* tp) {
+  constexpr size_t wbytes = warp_state_bytes<W>();
+  const bool in_smem = W <= 8;
+  tp->W = W;
+  tp->mode = MODE;
+  tp->nroots = nroots;
+  tp->fn = (const void*)k_enum<W, MODE>;
+  if (nroots == 0) return KC_OK;
+  tp->warps_per_block = W <= 4 ? 8 : 4;
+  tp->smem = in_smem ? wbytes * tp->warps_per_block : 0;
+  if (tp->smem > 48 * 1024)
+    KC_CUDA(cudaFuncSetAttribute(k_enum<W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp->smem));
+  int per_sm = 0;
+  KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enum<W, MODE>, tp->warps_per_block * 32, tp->smem));
+  per_sm = std::max(per_sm, 1);
+  uint64_t blocks = (uint64_t)ctx->num_sms * per_sm;
+  uint64_t need_blocks = (nroots + tp->warps_per_block - 1) / tp->warps_per_block;
+  blocks = std::max<uint64_t>(1, std::min(blocks, need_blocks));
+  if (!in_smem) {
+    uint64_t max_warps = std::max<uint64_t>(4, (1ull << 30) / wbytes);
+    blocks = std::max<uint64_t>(1, std::min<uint64_t>(blocks, max_warps / tp->warps_per_block));
+    tp->gstate_bytes = wbytes;
+  }
+  tp->blocks = blocks;
+  if (MODE == 2) {
+    uint64_t warps = blocks * tp->warps_per_block;
+    uint32_t cap = 1u << 12;
+    uint64_t budget = ctx->opts.memo_bytes ? ctx->opts.memo_bytes : (1ull << 30);
+    uint64_t per_entry = 4 + 4ull * W + 8;
+    while (cap > 256 && warps * cap * per_entry > budget / kTiers) cap >>= 1;
+    tp->memo_cap = cap;
+    tp->memo_bytes = warps * cap * per_entry;
+  }
+  return KC_OK;
+}
+
+template <int MODE>
+static int plan_all(kc_ctx* ctx, const uint32_t* hcnt, TierPlan* plans) {
+  // tiers wider than 8 words keep their state in global memory and count without the memo
+  constexpr int M16 = (MODE == 2) ? 0 : MODE;
+  KC_TRY((plan_tier<1, MODE>(ctx, hcnt[0], &plans[0])));
+  KC_TRY((plan_tier<2, MODE>(ctx, hcnt[1], &plans[1])));
+  KC_TRY((plan_tier<4, MODE>(ctx, hcnt[2], &plans[2])));
+  KC_TRY((plan_tier<8, MODE>(ctx, hcnt[3], &plans[3])));
+  KC_TRY((plan_tier<16, M16>(ctx, hcnt[4], &plans[4])));
+  KC_TRY((plan_tier<32, M16>(ctx, hcnt[5], &plans[5])));
+  return KC_OK;
+}
+
+int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s) {
+  kc_stats stt{};
+  uint32_t launches = 0, enum_launches = 0;
+  cudaEvent_t* ev = ctx->ev;
+  KC_CUDA(cudaEventRecord(ev[5], s));
+  KC_CUDA(cudaMemsetAsync(ctx->d_acc, 0, kAccSlots * sizeof(unsigned long long), s));
+  const uint32_t k = ea.k;
+  const uint32_t lo = ea.root_lo, hi = ea.root_hi;
+  if (k == 1) {
+    if (ea.mode == 1 && hi > lo) {
+      k_list_singletons<<<std::max<uint32_t>(1, std::min<uint32_t>((hi - lo + 255) / 256, ctx->num_sms * 8)), 256, 0,
+                          s>>>(g.vert, lo, hi, ea.d_buf, ea.cap, ctx->d_acc);
+      KC_CUDA(cudaGetLastError());
+      launches++;
+    }
+    KC_CUDA(cudaEventRecord(ev[6], s));
+    KC_CUDA(cudaEventRecord(ev[7], s));
+  } else {
+    uint32_t nr = hi > lo ? hi - lo : 0;
+    uint32_t lcap = std::max<uint32_t>(nr, 1);
+    void* lp = nullptr;
+    KC_TRY(scratch_get(ctx, kScrRoots, ((size_t)kTiers * lcap + 16) * sizeof(uint32_t), &lp));
+    uint32_t* lists = (uint32_t*)lp;
+    uint32_t* cnts = lists + (size_t)kTiers * lcap;
+    KC_CUDA(cudaMemsetAsync(cnts, 0, 16 * sizeof(uint32_t), s));
+    if (nr) {
+      unsigned blocks = std::max<uint32_t>(1, std::min<uint32_t>((nr + 255) / 256, ctx->num_sms * 8));
+      k_bin_roots<<<blocks, 256, 0, s>>>(g.orow, lo, hi, k - 1, lists, lcap, cnts, ctx->d_acc);
+      KC_CUDA(cudaGetLastError());
+      launches++;
+    }
+    uint32_t hcnt[16] = {0};
+    KC_CUDA(cudaMemcpyAsync(hcnt, cnts, sizeof(hcnt), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    KC_CUDA(cudaEventRecord(ev[6], s));
+    if (hcnt[kTiers] != 0) return KC_E_UNSUPPORTED;  // out-degree above the widest tier
+    // memo needs at least one level to split (k >= 3); k = 2 counts by popcount
+    const int mode = ea.mode == 1 ? 1 : ((ea.memo && k >= 3) ? 2 : 0);
+    TierPlan plans[kTiers];
+    if (mode == 1) KC_TRY(plan_all<1>(ctx, hcnt, plans));
+    else if (mode == 2) KC_TRY(plan_all<2>(ctx, hcnt, plans));
+    else KC_TRY(plan_all<0>(ctx, hcnt, plans));
+    // one scratch region for every tier's global state and memo tables
+    uint64_t total = 0;
+    uint64_t goff[kTiers], moff[kTiers];
+    for (int t = 0; t < kTiers; t++) {
+      goff[t] = total;
+      total += (plans[t].gstate_bytes * plans[t].blocks * std::max(plans[t].warps_per_block, 1) + 255) & ~255ull;
+      moff[t] = total;
+      total += (plans[t].memo_bytes + 255) & ~255ull;
+    }
+    void* base = nullptr;
+    if (total) KC_TRY(scratch_get(ctx, kScrEnum, total, &base));
+    EnumKArgs args{};
+    args.orow = g.orow;
+    args.ocol = g.ocol;
+    args.vert = g.vert;
+    args.k = k;
+    args.prune = ea.prune ? 1 : 0;
+    args.memo = ea.memo ? 1 : 0;
+    args.out = ea.d_buf;
+    args.cap = ea.cap;
+    args.acc = ctx->d_acc;
+    args.status = ctx->d_status;
+    // fork: every non-empty tier on its own stream, widest first
+    KC_CUDA(cudaEventRecord(ctx->ev_fork, s));
+    for (int t = kTiers - 1; t >= 0; t--) {
+      const TierPlan& tp = plans[t];
+      if (tp.nroots == 0) continue;
+      cudaStream_t ts = ctx->tier_stream[t];
+      KC_CUDA(cudaStreamWaitEvent(ts, ctx->ev_fork, 0));
+      EnumKArgs x = args;
+      x.roots = lists + (size_t)t * lcap;
+      x.nroots = tp.nroots;
+      x.qctr = (unsigned int*)&ctx->d_acc[kAccQueue0 + t];
+      if (tp.gstate_bytes) {
+        x.gstate = (uint8_t*)base + goff[t];
+        x.gstride = tp.gstate_bytes;
+      }
+      if (tp.memo_cap) {
+        uint64_t warps = tp.blocks * tp.warps_per_block;
+        uint8_t* mb = (uint8_t*)base + moff[t];
+        x.memo_vals = (unsigned long long*)mb;
+        x.memo_tags = (uint32_t*)(mb + warps * tp.memo_cap * 8);
+        x.memo_keys = (uint32_t*)(mb + warps * tp.memo_cap * 12);
+        x.memo_cap = tp.memo_cap;
+        KC_CUDA(cudaMemsetAsync(x.memo_tags, 0, warps * tp.memo_cap * 4, ts));
+      }
+      void* kargs[] = {&x};
+      KC_CUDA(cudaLaunchKernel(tp.fn, dim3((unsigned)tp.blocks), dim3(tp.warps_per_block * 32), kargs, tp.smem, ts));
+      launches++;
+      enum_launches++;
+      KC_CUDA(cudaEventRecord(ctx->ev_join[t], ts));
+      KC_CUDA(cudaStreamWaitEvent(s, ctx->ev_join[t], 0));
+    }
+    for (int t = 4; t < kTiers; t++) stt.roots_heavy += hcnt[t];
+    KC_CUDA(cudaEventRecord(ev[7], s));
+  }
+  KC_CUDA(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc, kAccSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaEventRecord(ev[8], s));
+  KC_CUDA(cudaEventSynchronize(ev[8]));
+  cudaEventElapsedTime(&stt.ms_bin, ev[5], ev[6]);
+  cudaEventElapsedTime(&stt.ms_enum, ev[6], ev[7]);
+  cudaEventElapsedTime(&stt.ms_total, ev[5], ev[8]);
+  stt.enum_launches = enum_launches;
+  stt.total_launches = launches;
+  stt.roots_total = ctx->h_acc[kAccRootsTotal];
+  stt.roots_pruned = ctx->h_acc[kAccRootsPruned];
+  stt.build_words = ctx->h_acc[kAccBuildWords];
+  stt.memo_hits = ctx->h_acc[kAccMemoHits];
+  stt.memo_inserts = ctx->h_acc[kAccMemoInserts];
+  stt.memo_full = ctx->h_acc[kAccMemoFull];
+  ctx->last = stt;
+  return KC_OK;
+}
+
+}  // namespace kc

@@ -1,0 +1,207 @@
+// kc_internal.cuh -- internal declarations shared by the libkc.so translation
+// units (device helpers, context and graph records, kernel launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "kclique.h"
+
+namespace kc {
+
+constexpr uint32_t kAlive = 0xFFFFFFFFu;
+constexpr int kWarp = 32;
+constexpr int kTiers = 6;  // enumerator widths 1, 2, 4, 8, 16, 32 words (out-degree <= 1024)
+
+// Device-side status bits (one uint32 per context, OR-ed by kernels).
+constexpr uint32_t kStBadGraph = 1u << 0;   // invalid id, unsorted row, self-loop, asymmetry
+constexpr uint32_t kStTimeout = 1u << 1;    // a bounded wait gave up
+constexpr uint32_t kStUnsupported = 1u << 2;
+constexpr uint32_t kStOverflow = 1u << 3;   // an internal capacity was exceeded
+
+// ------------------------------------------------------------ device helpers
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ uint32_t warp_min_u32(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  return v;
+}
+
+// SplitMix64 output function (Steele, Lea & Flood 2014), the clique hash's mixer.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded grid-wide barrier for a cooperative launch (all blocks co-resident).
+// Generation-counter sense; a block that waits longer than `limit_ns`
+// nanoseconds sets kStTimeout in *err and returns.  Returns false once any
+// block has reported a timeout, so every block leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, unsigned int nblocks,
+                                             unsigned long long limit_ns, unsigned int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned int g = *gen;
+    __threadfence();
+    unsigned int arrived = atomicAdd(count, 1u);
+    if (arrived == nblocks - 1) {
+      *count = 0;
+      __threadfence();
+      atomicAdd((unsigned int*)gen, 1u);
+    } else {
+      unsigned long long t0 = global_ns();
+      while (*gen == g) {
+        if (global_ns() - t0 > limit_ns) {
+          atomicOr(err, kStTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*((volatile unsigned int*)err) & kStTimeout) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------- host records
+struct DevGraph {
+  uint32_t n = 0;
+  uint64_t m = 0;             // undirected edges
+  uint32_t degeneracy = 0;
+  uint32_t max_out = 0;
+  uint32_t peel_rounds = 0;
+  uint32_t* core = nullptr;   // [n]
+  uint32_t* rank = nullptr;   // [n] rank of each original id
+  uint32_t* vert = nullptr;   // [n] original id of each rank
+  uint64_t* orow = nullptr;   // [n+1] DAG CSR in rank space
+  uint32_t* ocol = nullptr;   // [m]
+};
+
+struct Scratch {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace kc
+
+struct kc_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  cudaStream_t own_stream = nullptr;
+  kc_opts opts{};
+  uint32_t next_handle = 1;
+  std::unordered_map<uint32_t, kc::DevGraph> graphs;
+  std::vector<kc::Scratch> scratch;       // reusable device work buffers, by slot
+  uint32_t* d_status = nullptr;           // device status bits
+  unsigned long long* d_acc = nullptr;    // device accumulators (count, checksum, written, stats ...)
+  unsigned long long* h_acc = nullptr;    // pinned host mirror
+  cudaEvent_t ev[16] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kc::kTiers] = {};
+  cudaStream_t tier_stream[kc::kTiers] = {};
+  kc_stats last{};
+  kc_upload_stats last_up{};
+  std::string last_error;
+};
+
+namespace kc {
+
+// Accumulator slots in ctx->d_acc.
+enum AccSlot : int {
+  kAccCount = 0,
+  kAccChecksum,
+  kAccWritten,
+  kAccRootsTotal,
+  kAccRootsPruned,
+  kAccRootsHeavy,
+  kAccBuildWords,
+  kAccMemoHits,
+  kAccMemoInserts,
+  kAccMemoFull,
+  kAccQueue0,      // work-queue counters (one per enumerator launch)
+  kAccQueueLast = kAccQueue0 + 15,
+  kAccSlots
+};
+
+// Scratch slots.
+enum ScratchSlot : int {
+  kScrA = 0, kScrB, kScrC, kScrD, kScrE, kScrF, kScrG, kScrScan, kScrSort, kScrSortList, kScrEnum, kScrMemo,
+  kScrRoots, kScrPeel,
+  kScrSlots
+};
+
+int scratch_get(kc_ctx* ctx, int slot, size_t bytes, void** out);
+int cuda_fail(kc_ctx* ctx, cudaError_t e, const char* what);
+
+#define KC_CUDA(call)                                        \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return ::kc::cuda_fail(ctx, _e, #call); \
+  } while (0)
+
+#define KC_TRY(call)              \
+  do {                            \
+    int _s = (call);              \
+    if (_s != KC_OK) return _s;   \
+  } while (0)
+
+// ----------------------------------------------------------- launch helpers
+// Exclusive scan of n uint32 counts into n+1 uint64 offsets (out[n] = total).
+int exclusive_scan_u32_to_u64(kc_ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t s,
+                              uint32_t* launches);
+// Sort each row [ptr[r], ptr[r+1]) of data ascending (uint32 keys).  When
+// ucount != nullptr also moves each row's distinct keys to the row front and
+// writes their number to ucount[r].
+int segmented_sort(kc_ctx* ctx, uint32_t* data, const uint64_t* ptr, uint32_t rows, uint64_t total, uint32_t max_row,
+                   uint32_t* ucount, cudaStream_t s, uint32_t* launches);
+
+// Upload pipeline (kc_prep.cu).
+int prep_graph(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr, const uint32_t* col, uint32_t flags,
+               DevGraph* g, cudaStream_t s);
+
+// Enumeration (kc_enum.cu).  mode 0: count, mode 1: list.
+struct EnumArgs {
+  uint32_t k = 0;
+  int mode = 0;
+  uint32_t root_lo = 0, root_hi = 0;
+  uint32_t* d_buf = nullptr;
+  uint64_t cap = 0;
+  bool memo = true;
+  bool prune = true;
+};
+int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& a, cudaStream_t s);
+
+}  // namespace kc

@@ -1,0 +1,300 @@
+"""Python binding of libkc.so (include/kclique.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+graph work of its own: the path runs in the library's CUDA kernels.  PyTorch
+is used only for device memory and streams (tensors on the GPU are passed as
+raw device pointers).  If libkc.so cannot be built or loaded, ``load()``
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from functools import lru_cache
+
+import numpy as np
+
+from . import build as _build
+
+KC_OK = 0
+KC_E_INVALID_ARG = 1
+KC_E_INVALID_GRAPH = 2
+KC_E_OOM = 3
+KC_E_CAPACITY = 4
+KC_E_DEVICE_TIMEOUT = 5
+KC_E_CUDA = 6
+KC_E_BUSY = 7
+KC_E_UNSUPPORTED = 8
+KC_E_NOT_FOUND = 9
+
+KC_HOST_PTRS = 0x1
+KC_DEVICE_PTRS = 0x2
+KC_CANONICALIZE = 0x4
+
+KC_MAX_K = 64
+KC_MAX_OUTDEG = 1024
+
+# Every entry point include/kclique.h declares (checked by the CPU tests).
+EXPORTS = (
+    "kc_create", "kc_destroy", "kc_upload", "kc_free_graph", "kc_graph_info_get", "kc_export_dag",
+    "kc_count", "kc_list", "kc_list_range", "kc_last_stats", "kc_last_upload_stats", "kc_strerror",
+    "kc_last_error",
+)
+
+
+class KcError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        name = kc_strerror(status) if status else "KC_OK"
+        super().__init__(f"{what}: {name}" if what else name)
+
+
+class kc_opts(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("no_memo", ctypes.c_uint32),
+        ("no_prune", ctypes.c_uint32),
+        ("split_threshold", ctypes.c_uint32),
+        ("memo_bytes", ctypes.c_uint64),
+        ("spin_limit", ctypes.c_uint64),
+    ]
+
+
+class kc_graph_info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint32),
+        ("degeneracy", ctypes.c_uint32),
+        ("m", ctypes.c_uint64),
+        ("max_out_degree", ctypes.c_uint32),
+        ("peel_rounds", ctypes.c_uint32),
+    ]
+
+
+class kc_stats(ctypes.Structure):
+    _fields_ = [
+        ("ms_bin", ctypes.c_float),
+        ("ms_enum", ctypes.c_float),
+        ("ms_total", ctypes.c_float),
+        ("enum_launches", ctypes.c_uint32),
+        ("total_launches", ctypes.c_uint32),
+        ("roots_total", ctypes.c_uint64),
+        ("roots_pruned", ctypes.c_uint64),
+        ("roots_heavy", ctypes.c_uint64),
+        ("build_words", ctypes.c_uint64),
+        ("memo_hits", ctypes.c_uint64),
+        ("memo_inserts", ctypes.c_uint64),
+        ("memo_full", ctypes.c_uint64),
+    ]
+
+
+class kc_upload_stats(ctypes.Structure):
+    _fields_ = [
+        ("ms_copy", ctypes.c_float),
+        ("ms_canon", ctypes.c_float),
+        ("ms_peel", ctypes.c_float),
+        ("ms_orient", ctypes.c_float),
+        ("ms_total", ctypes.c_float),
+        ("launches", ctypes.c_uint32),
+    ]
+
+
+def _struct_dict(s) -> dict:
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+@lru_cache(maxsize=1)
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libkc.so (building it first if the sources changed)."""
+    path = path or _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libkc.so missing at {path}")
+    lib = ctypes.CDLL(path)
+    P, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    pu64 = ctypes.POINTER(u64)
+    sig = {
+        "kc_create": (i32, [ctypes.POINTER(P), i32, ctypes.POINTER(kc_opts)]),
+        "kc_destroy": (i32, [P]),
+        "kc_upload": (i32, [P, u32, P, P, u32, ctypes.POINTER(u32), P]),
+        "kc_free_graph": (i32, [P, u32]),
+        "kc_graph_info_get": (i32, [P, u32, ctypes.POINTER(kc_graph_info)]),
+        "kc_export_dag": (i32, [P, u32, P, P, P, P]),
+        "kc_count": (i32, [P, u32, u32, pu64, P]),
+        "kc_list": (i32, [P, u32, u32, P, u64, pu64, pu64, pu64, P]),
+        "kc_list_range": (i32, [P, u32, u32, u32, u32, P, u64, pu64, pu64, pu64, P]),
+        "kc_last_stats": (i32, [P, ctypes.POINTER(kc_stats)]),
+        "kc_last_upload_stats": (i32, [P, ctypes.POINTER(kc_upload_stats)]),
+        "kc_strerror": (ctypes.c_char_p, [i32]),
+        "kc_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+def _check(st: int, what: str):
+    if st != KC_OK:
+        raise KcError(st, what)
+
+
+def _ptr(x):
+    """Raw pointer of a numpy array (host) or a torch tensor (host or device)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------- C-ABI mirror
+def kc_strerror(status: int) -> str:
+    return load().kc_strerror(int(status)).decode()
+
+
+def kc_create(device: int = 0, no_memo: bool = False, no_prune: bool = False, memo_bytes: int = 0,
+              spin_limit: int = 0) -> int:
+    o = kc_opts(ctypes.sizeof(kc_opts), int(no_memo), int(no_prune), 0, int(memo_bytes), int(spin_limit))
+    h = ctypes.c_void_p()
+    _check(load().kc_create(ctypes.byref(h), int(device), ctypes.byref(o)), "kc_create")
+    return h.value
+
+
+def kc_destroy(ctx: int) -> None:
+    _check(load().kc_destroy(ctypes.c_void_p(ctx)), "kc_destroy")
+
+
+def kc_upload(ctx: int, n: int, rowptr, col, flags: int, stream=None) -> int:
+    g = ctypes.c_uint32(0)
+    st = load().kc_upload(ctypes.c_void_p(ctx), int(n), _ptr(rowptr), _ptr(col), int(flags), ctypes.byref(g),
+                          _stream(stream))
+    _check(st, "kc_upload")
+    return int(g.value)
+
+
+def kc_free_graph(ctx: int, g: int) -> None:
+    _check(load().kc_free_graph(ctypes.c_void_p(ctx), int(g)), "kc_free_graph")
+
+
+def kc_graph_info_get(ctx: int, g: int) -> dict:
+    info = kc_graph_info()
+    _check(load().kc_graph_info_get(ctypes.c_void_p(ctx), int(g), ctypes.byref(info)), "kc_graph_info_get")
+    return _struct_dict(info)
+
+
+def kc_export_dag(ctx: int, g: int):
+    info = kc_graph_info_get(ctx, g)
+    n, m = info["n"], info["m"]
+    core = np.zeros(max(n, 1), dtype=np.uint32)
+    rank = np.zeros(max(n, 1), dtype=np.uint32)
+    orow = np.zeros(n + 1, dtype=np.uint64)
+    ocol = np.zeros(max(m, 1), dtype=np.uint32)
+    _check(load().kc_export_dag(ctypes.c_void_p(ctx), int(g), _ptr(core), _ptr(rank), _ptr(orow), _ptr(ocol)),
+           "kc_export_dag")
+    return core[:n], rank[:n], orow, ocol[:m]
+
+
+def kc_count(ctx: int, g: int, k: int, stream=None) -> int:
+    c = ctypes.c_uint64(0)
+    _check(load().kc_count(ctypes.c_void_p(ctx), int(g), int(k), ctypes.byref(c), _stream(stream)), "kc_count")
+    return int(c.value)
+
+
+def kc_list(ctx: int, g: int, k: int, d_buf=None, cap: int = 0, stream=None, allow_capacity: bool = False):
+    """Returns (written, total, checksum); d_buf is a device tensor of >= cap*k 32-bit ints."""
+    w, t, s = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    st = load().kc_list(ctypes.c_void_p(ctx), int(g), int(k), _ptr(d_buf), int(cap), ctypes.byref(w), ctypes.byref(t),
+                        ctypes.byref(s), _stream(stream))
+    if not (allow_capacity and st == KC_E_CAPACITY):
+        _check(st, "kc_list")
+    return int(w.value), int(t.value), int(s.value)
+
+
+def kc_list_range(ctx: int, g: int, k: int, root_lo: int, root_hi: int, d_buf=None, cap: int = 0, stream=None,
+                  allow_capacity: bool = False):
+    w, t, s = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    st = load().kc_list_range(ctypes.c_void_p(ctx), int(g), int(k), int(root_lo), int(root_hi), _ptr(d_buf), int(cap),
+                              ctypes.byref(w), ctypes.byref(t), ctypes.byref(s), _stream(stream))
+    if not (allow_capacity and st == KC_E_CAPACITY):
+        _check(st, "kc_list_range")
+    return int(w.value), int(t.value), int(s.value)
+
+
+def kc_last_stats(ctx: int) -> dict:
+    s = kc_stats()
+    _check(load().kc_last_stats(ctypes.c_void_p(ctx), ctypes.byref(s)), "kc_last_stats")
+    return _struct_dict(s)
+
+
+def kc_last_upload_stats(ctx: int) -> dict:
+    s = kc_upload_stats()
+    _check(load().kc_last_upload_stats(ctypes.c_void_p(ctx), ctypes.byref(s)), "kc_last_upload_stats")
+    return _struct_dict(s)
+
+
+def kc_last_error(ctx: int) -> str:
+    return load().kc_last_error(ctypes.c_void_p(ctx)).decode()
+
+
+# ------------------------------------------------------- convenience
+class Context:
+    """Owns a kc_ctx; methods forward to the C entry points."""
+
+    def __init__(self, device: int = 0, **opts):
+        self.h = kc_create(device, **opts)
+
+    def close(self):
+        if self.h:
+            kc_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def upload_host(self, n: int, rowptr: np.ndarray, col: np.ndarray, canonicalize: bool = False, stream=None) -> int:
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.uint64)
+        col = np.ascontiguousarray(col, dtype=np.uint32)
+        if col.size == 0:
+            col = np.zeros(1, dtype=np.uint32)
+        flags = KC_HOST_PTRS | (KC_CANONICALIZE if canonicalize else 0)
+        return kc_upload(self.h, n, rowptr, col, flags, stream)
+
+    def upload_device(self, n: int, rowptr, col, canonicalize: bool = False, stream=None) -> int:
+        flags = KC_DEVICE_PTRS | (KC_CANONICALIZE if canonicalize else 0)
+        return kc_upload(self.h, n, rowptr, col, flags, stream)
+
+    def free(self, g: int):
+        kc_free_graph(self.h, g)
+
+    def info(self, g: int) -> dict:
+        return kc_graph_info_get(self.h, g)
+
+    def count(self, g: int, k: int, stream=None) -> int:
+        return kc_count(self.h, g, k, stream)
+
+    def list(self, g: int, k: int, d_buf=None, cap: int = 0, stream=None, allow_capacity: bool = False):
+        return kc_list(self.h, g, k, d_buf, cap, stream, allow_capacity)
+
+    def list_range(self, g: int, k: int, lo: int, hi: int, d_buf=None, cap: int = 0, stream=None,
+                   allow_capacity: bool = False):
+        return kc_list_range(self.h, g, k, lo, hi, d_buf, cap, stream, allow_capacity)
+
+    def stats(self) -> dict:
+        return kc_last_stats(self.h)
+
+    def upload_stats(self) -> dict:
+        return kc_last_upload_stats(self.h)
+
+    def export_dag(self, g: int):
+        return kc_export_dag(self.h, g)

@@ -1,0 +1,390 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle.
+
+Integer work, so the bar is bit-exact: counts, checksums, core numbers and
+listed tuples must equal the oracle's.  Where several outputs are correct
+(the DAG orientation, the order of listed tuples) the unique parts are
+compared and the rest is checked for validity.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_00317_gb300 import graphgen as gg
+from paper_2502_00317_gb300 import kclique as kc
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = kc.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx_plain():
+    c = kc.Context(0, no_memo=True, no_prune=True)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx_memo_only():
+    c = kc.Context(0, no_prune=True)
+    yield c
+    c.close()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _list_all(c, g, k, total):
+    torch = _torch()
+    buf = torch.empty(max(total * k, 1), dtype=torch.int32, device="cuda")
+    w, t, s = c.list(g, k, buf, total)
+    torch.cuda.synchronize()
+    arr = buf[: w * k].cpu().numpy().view(np.uint32).reshape(w, k)
+    return arr, t, s
+
+
+def _check_graph(c, g, og, ks, listing=True):
+    h = c.upload_host(g.n, g.rowptr, g.col, canonicalize=not g.canonical)
+    try:
+        info = c.info(h)
+        assert info["m"] == og.m
+        assert info["degeneracy"] == og.degeneracy
+        for k in ks:
+            want_c, want_s = og.checksum(k)
+            assert c.count(h, k) == want_c, ("count", g.name, k)
+            if listing:
+                arr, t, s = _list_all(c, h, k, want_c)
+                assert t == want_c and s == want_s, ("list", g.name, k)
+                assert arr.shape[0] == want_c
+                if want_c and want_c <= 200000:
+                    got = np.unique(arr, axis=0)
+                    assert got.shape[0] == want_c  # no tuple twice
+                    exp, _, _ = og.list(k)
+                    assert np.array_equal(got, np.unique(exp, axis=0))
+    finally:
+        c.free(h)
+
+
+def _fig2():
+    d = json.load(open(os.path.join(GOLD, "fig2_dag.json")))
+    out = {int(u): v for u, v in d["out"].items()}
+    a = [u for u in out for v in out[u]]
+    b = [v for u in out for v in out[u]]
+    return d, gg.csr_from_pairs(d["n"], np.array(a), np.array(b))
+
+
+# ------------------------------------------------------------ worked example
+def test_fig2_dag(ctx):
+    d, g = _fig2()
+    og = oracle.OracleGraph.from_graph(g)
+    h = ctx.upload_host(g.n, g.rowptr, g.col)
+    assert ctx.count(h, 4) == d["k4_count"] == 14
+    arr, t, s = _list_all(ctx, h, 4, 14)
+    got = {tuple(r) for r in arr.tolist()}
+    for cl in d["k4_first_cliques"]:
+        assert tuple(cl) in got
+    assert [ctx.count(h, k) for k in range(1, 7)] == [og.count(k)[0] for k in range(1, 7)]
+    ctx.free(h)
+    _check_graph(ctx, g, og, range(1, 7))
+
+
+# ---------------------------------------------------------- closed forms
+@pytest.mark.parametrize("n", [2, 5, 31, 32, 33, 64, 65, 100, 129, 200])
+def test_complete_graphs(ctx, n):
+    g = gg.complete(n)
+    h = ctx.upload_host(g.n, g.rowptr, g.col)
+    try:
+        for k in sorted({1, 2, 3, 4, 5, 6, 9, min(n, 12), n, n + 1} - {0}):
+            if k > kc.KC_MAX_K:
+                continue
+            if n >= 100 and 7 <= k < n - 3:
+                continue  # C(n, k) too large to enumerate in a test
+            assert ctx.count(h, k) == oracle.binom(n, k), (n, k)
+    finally:
+        ctx.free(h)
+
+
+@pytest.mark.parametrize("n,r", [(10, 3), (17, 4), (24, 5), (30, 7), (40, 10), (70, 6)])
+def test_turan_graphs(ctx, n, r):
+    g = gg.turan(n, r)
+    sizes = [len(range(i, n, r)) for i in range(r)]
+    h = ctx.upload_host(g.n, g.rowptr, g.col)
+    try:
+        for k in range(1, r + 3):
+            assert ctx.count(h, k) == oracle.elementary_symmetric(sizes, k), (n, r, k)
+    finally:
+        ctx.free(h)
+
+
+def test_disjoint_cliques(ctx):
+    sizes = [3, 7, 11, 20, 33, 47, 60, 1, 5]
+    g = gg.disjoint_cliques(sizes)
+    h = ctx.upload_host(g.n, g.rowptr, g.col)
+    try:
+        for k in range(1, 11):
+            assert ctx.count(h, k) == sum(oracle.binom(s, k) for s in sizes)
+    finally:
+        ctx.free(h)
+
+
+# ----------------------------------------------------- random vs oracle
+@pytest.mark.parametrize("seed", range(10))
+def test_tiny_random_vs_brute_force(ctx, seed):
+    n = 8 + seed
+    g = gg.er_gnp(n, [0.2, 0.4, 0.6, 0.8, 0.95][seed % 5], seed)
+    adj = oracle.adjacency_sets(g.n, g.rowptr, g.col)
+    h = ctx.upload_host(g.n, g.rowptr, g.col)
+    try:
+        for k in range(1, 9):
+            bf = oracle.brute_force_cliques(g.n, adj, k)
+            assert ctx.count(h, k) == len(bf)
+            if bf:
+                arr, t, s = _list_all(ctx, h, k, len(bf))
+                assert sorted(map(tuple, arr.tolist())) == bf
+                assert s == sum(oracle.clique_hash(c) for c in bf) % (1 << 64)
+    finally:
+        ctx.free(h)
+
+
+@pytest.mark.parametrize("n,p,seed", [(300, 0.3, 1), (500, 0.12, 2), (1000, 0.05, 3), (150, 0.6, 4)])
+def test_medium_random_vs_oracle(ctx, n, p, seed):
+    g = gg.er_gnp(n, p, seed)
+    og = oracle.OracleGraph.from_graph(g)
+    _check_graph(ctx, g, og, [3, 4, 5, 6], listing=True)
+
+
+def test_er_2000_config_vs_golden(ctx):
+    """Erdos-Renyi G(2000, 0.01), seed 0: counts and checksums for k = 3, 4, 5."""
+    gold = json.load(open(os.path.join(GOLD, "config_results.json")))
+    g = gg.config_er_small()
+    h = ctx.upload_host(g.n, g.rowptr, g.col)
+    try:
+        for k in (3, 4, 5):
+            want = gold[f"er_2000_0.01_seed0_k{k}"]
+            assert want["fingerprint"] == g.fingerprint()
+            assert ctx.count(h, k) == want["count"]
+            w, t, s = ctx.list(h, k, None, 0)
+            assert (t, s) == (want["count"], want["checksum"])
+    finally:
+        ctx.free(h)
+
+
+def test_chung_lu_small_tiers(ctx, ctx_plain, ctx_memo_only):
+    """Power-law background + planted cliques: every width tier, memo and pruning on/off."""
+    g = gg.chung_lu_planted(n=20000, n_cliques=40, seed=1)
+    og = oracle.OracleGraph.from_graph(g)
+    hs = [c.upload_host(g.n, g.rowptr, g.col) for c in (ctx, ctx_plain, ctx_memo_only)]
+    try:
+        for k in (3, 4, 5, 6, 7):
+            want = og.count(k)[0]
+            for c, h in zip((ctx, ctx_plain, ctx_memo_only), hs):
+                assert c.count(h, k) == want, (k, c)
+        for k in (4, 5):
+            want_c, want_s = og.checksum(k)
+            for c, h in zip((ctx, ctx_plain), hs[:2]):
+                w, t, s = c.list(h, k, None, 0)
+                assert (t, s) == (want_c, want_s)
+    finally:
+        for c, h in zip((ctx, ctx_plain, ctx_memo_only), hs):
+            c.free(h)
+
+
+# ------------------------------------------------- peel / orient (a2, a3)
+@pytest.mark.parametrize("maker", [
+    lambda: gg.er_gnp(3000, 0.004, 7),
+    lambda: gg.chung_lu_planted(n=20000, n_cliques=40, seed=1),
+    lambda: gg.complete(70),
+    lambda: gg.rgg_torus(5000, 30.0, seed=5),
+])
+def test_core_numbers_and_dag(ctx, maker):
+    g = maker()
+    og = oracle.OracleGraph.from_graph(g)
+    h = ctx.upload_host(g.n, g.rowptr, g.col)
+    try:
+        core, rank, orow, ocol = ctx.export_dag(h)
+        info = ctx.info(h)
+        # core numbers do not depend on tie-breaking: bit-exact
+        assert np.array_equal(core, og.core_numbers())
+        assert info["degeneracy"] == og.degeneracy
+        # the order is a permutation and a degeneracy order: out-degree <= delta
+        assert np.array_equal(np.sort(rank), np.arange(g.n, dtype=np.uint32))
+        outdeg = np.diff(orow.astype(np.int64))
+        assert outdeg.max(initial=0) == info["max_out_degree"] <= og.degeneracy
+        # the DAG holds each undirected edge once, oriented to the higher rank, rows sorted
+        assert int(orow[-1]) == og.m
+        src = np.repeat(np.arange(g.n, dtype=np.int64), outdeg)
+        dst = ocol.astype(np.int64)
+        assert np.all(dst > src)
+        if dst.size:
+            same_row = src[1:] == src[:-1]
+            assert np.all(dst[1:][same_row] > dst[:-1][same_row])
+        vert = np.empty(g.n, dtype=np.int64)
+        vert[rank.astype(np.int64)] = np.arange(g.n)
+        a, b = vert[src], vert[dst]
+        got = np.sort(np.minimum(a, b) * g.n + np.maximum(a, b))
+        ea, eb = gg.edges_of(g)
+        want = np.sort(ea.astype(np.int64) * g.n + eb)
+        assert np.array_equal(got, want)
+        # vertices of lower core come first in the order
+        assert np.all(np.diff(core[vert].astype(np.int64)) >= 0)
+    finally:
+        ctx.free(h)
+
+
+# -------------------------------------------------------- canonicalisation
+def test_canonicalise_raw_rmat(ctx):
+    g = gg.rmat(scale=12, edge_factor=16, seed=2)
+    assert not g.canonical
+    og = oracle.OracleGraph.from_graph(g)
+    h = ctx.upload_host(g.n, g.rowptr, g.col, canonicalize=True)
+    try:
+        info = ctx.info(h)
+        assert info["m"] == og.m and info["degeneracy"] == og.degeneracy
+        core, rank, orow, ocol = ctx.export_dag(h)
+        assert np.array_equal(core, og.core_numbers())
+        for k in (3, 4, 5, 6):
+            want_c, want_s = og.checksum(k)
+            assert ctx.count(h, k) == want_c
+            w, t, s = ctx.list(h, k, None, 0)
+            assert (t, s) == (want_c, want_s)
+    finally:
+        ctx.free(h)
+
+
+def test_canonicalise_hub_rows(ctx):
+    """Rows longer than one shared-memory sort tile (4096 keys) with repeats."""
+    rng = np.random.default_rng(3)
+    n = 9000
+    hub = np.zeros(30000, dtype=np.int64)
+    other = rng.integers(0, n, 30000)
+    extra_a = rng.integers(0, n, 20000)
+    extra_b = rng.integers(0, n, 20000)
+    g = gg.raw_csr_from_pairs(n, np.concatenate([hub, extra_a, other[:50]]),
+                              np.concatenate([other, extra_b, hub[:50]]))
+    og = oracle.OracleGraph.from_graph(g)
+    h = ctx.upload_host(g.n, g.rowptr, g.col, canonicalize=True)
+    try:
+        assert ctx.info(h)["m"] == og.m
+        core, _, _, _ = ctx.export_dag(h)
+        assert np.array_equal(core, og.core_numbers())
+        for k in (3, 4):
+            assert ctx.list(h, k, None, 0)[1:] == og.checksum(k)
+    finally:
+        ctx.free(h)
+
+
+def test_invalid_graphs_rejected(ctx):
+    # asymmetric
+    rowptr = np.array([0, 1, 1], dtype=np.uint64)
+    col = np.array([1], dtype=np.uint32)
+    with pytest.raises(kc.KcError) as e:
+        ctx.upload_host(2, rowptr, col)
+    assert e.value.status == kc.KC_E_INVALID_GRAPH
+    # self-loop
+    with pytest.raises(kc.KcError):
+        ctx.upload_host(1, np.array([0, 1], dtype=np.uint64), np.array([0], dtype=np.uint32))
+    # unsorted row
+    with pytest.raises(kc.KcError):
+        ctx.upload_host(3, np.array([0, 2, 3, 4], dtype=np.uint64), np.array([2, 1, 0, 0], dtype=np.uint32))
+    # id out of range, also with canonicalisation
+    with pytest.raises(kc.KcError):
+        ctx.upload_host(2, np.array([0, 1, 1], dtype=np.uint64), np.array([7], dtype=np.uint32), canonicalize=True)
+    # the context stays usable
+    g = gg.complete(6)
+    h = ctx.upload_host(g.n, g.rowptr, g.col)
+    assert ctx.count(h, 3) == 20
+    ctx.free(h)
+
+
+# --------------------------------------------------------- list semantics
+def test_list_capacity_and_ranges(ctx):
+    g = gg.er_gnp(400, 0.15, 11)
+    og = oracle.OracleGraph.from_graph(g)
+    want_c, want_s = og.checksum(4)
+    torch = _torch()
+    h = ctx.upload_host(g.n, g.rowptr, g.col)
+    try:
+        cap = want_c // 3
+        buf = torch.empty(cap * 4, dtype=torch.int32, device="cuda")
+        w, t, s = ctx.list(h, 4, buf, cap, allow_capacity=True)
+        assert (w, t, s) == (cap, want_c, want_s)
+        arr = buf.cpu().numpy().view(np.uint32).reshape(cap, 4)
+        full = {tuple(r) for r in og.list(4)[0].tolist()}
+        assert len({tuple(r) for r in arr.tolist()}) == cap
+        assert all(tuple(r) in full for r in arr.tolist())
+        with pytest.raises(kc.KcError) as e:
+            ctx.list(h, 4, buf, cap)
+        assert e.value.status == kc.KC_E_CAPACITY
+        cuts = [0, 1, 57, 200, 201, 399, 400]
+        tot, chk = 0, 0
+        for lo, hi in zip(cuts, cuts[1:]):
+            _, t, s = ctx.list_range(h, 4, lo, hi)
+            tot += t
+            chk = (chk + s) % (1 << 64)
+        assert (tot, chk) == (want_c, want_s)
+    finally:
+        ctx.free(h)
+
+
+def test_edge_cases(ctx):
+    g = gg.csr_from_pairs(5, np.zeros(0), np.zeros(0))
+    h = ctx.upload_host(g.n, g.rowptr, g.col)
+    assert [ctx.count(h, k) for k in (1, 2, 3)] == [5, 0, 0]
+    assert ctx.list(h, 1, None, 0)[1] == 5
+    ctx.free(h)
+    g = gg.complete(7)
+    h = ctx.upload_host(g.n, g.rowptr, g.col)
+    assert ctx.count(h, 7) == 1 and ctx.count(h, 8) == 0
+    for bad, code in ((0, kc.KC_E_INVALID_ARG), (kc.KC_MAX_K + 1, kc.KC_E_UNSUPPORTED)):
+        with pytest.raises(kc.KcError) as e:
+            ctx.count(h, bad)
+        assert e.value.status == code
+    k1 = ctx.list(h, 1, None, 0)
+    assert k1[1] == 7 and k1[2] == sum(oracle.clique_hash([v]) for v in range(7)) % (1 << 64)
+    ctx.free(h)
+    with pytest.raises(kc.KcError) as e:
+        ctx.count(12345, 3)
+    assert e.value.status == kc.KC_E_NOT_FOUND
+
+
+def test_device_pointer_upload(ctx):
+    torch = _torch()
+    g = gg.er_gnp(500, 0.1, 9)
+    og = oracle.OracleGraph.from_graph(g)
+    rp = torch.from_numpy(g.rowptr.view(np.int64)).cuda()
+    cl = torch.from_numpy(g.col.view(np.int32)).cuda()
+    h = ctx.upload_device(g.n, rp, cl)
+    try:
+        assert ctx.count(h, 4) == og.count(4)[0]
+    finally:
+        ctx.free(h)
+
+
+# ------------------------------------------------------- full-size configs
+def test_chung_lu_full_size_vs_golden(ctx):
+    """Chung-Lu n = 1e6 + 2000 planted cliques: counts for every k the oracle has finished."""
+    gold = json.load(open(os.path.join(GOLD, "config_results.json")))
+    keys = sorted(k for k in gold if k.startswith("chung_lu_1e6_2000cliques_seed1_k"))
+    assert keys
+    g = gg.config_chung_lu()
+    assert gold[keys[0]]["fingerprint"] == g.fingerprint()
+    h = ctx.upload_host(g.n, g.rowptr, g.col)
+    try:
+        info = ctx.info(h)
+        assert info["m"] == gold[keys[0]]["m"] and info["degeneracy"] == gold[keys[0]]["degeneracy"]
+        for key in keys:
+            k = int(key.rsplit("_k", 1)[1])
+            assert ctx.count(h, k) == gold[key]["count"], k
+    finally:
+        ctx.free(h)

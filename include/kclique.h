@@ -154,7 +154,8 @@ int kc_count(kc_ctx* ctx, kc_graph g, uint32_t k, uint64_t* count, void* stream)
  * mix(0x9E3779B97F4A7C15 ^ k), then h = mix(h ^ id) for each id ascending).
  * total and checksum always cover every clique; when total > cap the call
  * still fills d_buf with an unspecified subset and returns KC_E_CAPACITY.
- * cap may be 0 (d_buf may then be NULL) to get total and checksum only.
+ * cap may be 0 (d_buf may then be NULL) to get total and checksum only;
+ * that call returns KC_OK.
  * Synchronises the stream.
  */
 int kc_list(kc_ctx* ctx, kc_graph g, uint32_t k, uint32_t* d_buf, uint64_t cap, uint64_t* written,

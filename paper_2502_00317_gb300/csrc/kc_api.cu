@@ -247,7 +247,7 @@ static int enum_common(kc_ctx* ctx, kc_graph h, uint32_t k, int mode, uint32_t l
   if (checksum) *checksum = ctx->h_acc[kAccChecksum];
   uint64_t wr = std::min<uint64_t>(tot, ea.cap);
   if (written) *written = wr;
-  if (mode == 1 && tot > ea.cap) return KC_E_CAPACITY;
+  if (mode == 1 && ea.cap > 0 && tot > ea.cap) return KC_E_CAPACITY;  // cap 0: total and checksum only
   return KC_OK;
 }
 

@@ -83,6 +83,9 @@ typedef struct kc_stats {
   uint64_t memo_hits;      /* device trie hits */
   uint64_t memo_inserts;   /* device trie insertions */
   uint64_t memo_full;      /* insertions refused because a table was full */
+  uint64_t memo_frames;    /* memoised frames opened (device trie walks) */
+  float ms_tier[6];        /* device time of each width tier (1, 2, 4, 8, 16, 32 words) */
+  uint32_t roots_tier[6];  /* roots in each width tier */
 } kc_stats;
 
 /* Per-stage device times of the last kc_upload (CUDA events). */

@@ -111,6 +111,8 @@ int kc_create(kc_ctx** out, int device, const kc_opts* opts) {
       return fail(e, "cudaStreamCreate");
     if ((e = cudaEventCreateWithFlags(&ctx->ev_join[t], cudaEventDisableTiming)) != cudaSuccess)
       return fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&ctx->ev_tier0[t])) != cudaSuccess) return fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&ctx->ev_tier1[t])) != cudaSuccess) return fail(e, "cudaEventCreate");
   }
   if ((e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming)) != cudaSuccess)
     return fail(e, "cudaEventCreate");
@@ -143,6 +145,8 @@ int kc_destroy(kc_ctx* ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   for (int t = 0; t < kTiers; t++) {
     if (ctx->ev_join[t]) cudaEventDestroy(ctx->ev_join[t]);
+    if (ctx->ev_tier0[t]) cudaEventDestroy(ctx->ev_tier0[t]);
+    if (ctx->ev_tier1[t]) cudaEventDestroy(ctx->ev_tier1[t]);
     if (ctx->tier_stream[t]) cudaStreamDestroy(ctx->tier_stream[t]);
   }
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);

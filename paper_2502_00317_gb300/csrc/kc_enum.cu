@@ -53,6 +53,16 @@ struct EnumKArgs {
   unsigned long long* memo_vals;
   uint32_t memo_cap;          // entries per warp (power of two)
   uint32_t* status;
+  // split path (heavy roots): arena of published roots and a task queue
+  uint32_t split_wedges;      // 0: never split
+  int split_min_d;
+  uint8_t* arena;
+  unsigned long long arena_units;  // 16-byte units
+  unsigned long long* arena_used;
+  unsigned long long* tasks;
+  unsigned long long task_cap;
+  unsigned long long* task_used;
+  unsigned long long* task_head;
 };
 
 // Per-warp working state, carved from shared or global memory.
@@ -240,424 +250,742 @@ __device__ __forceinline__ int select_bit(const uint32_t (&c)[W], int j) {
   return -1;
 }
 
-// ----------------------------------------------------------- the kernel
+// Triangles of G[S] (the 3-cliques of S), lane-partial: lanes take the
+// vertices v of S that can start a 3-clique (r_v >= 3) and each counts the
+// edges of S ∩ row(v) on its own.
+template <int W>
+__device__ __forceinline__ uint32_t tri_partial(const uint32_t (&S)[W], const uint32_t* rows, const uint32_t* m3) {
+  const uint32_t lane = lane_id();
+  uint32_t acc = 0;
+#pragma unroll
+  for (int w = 0; w < W; w++) {
+    if (((S[w] & m3[w]) >> lane) & 1u) {
+      const uint32_t* rv = rows + (size_t)((w << 5) + lane) * W;
+      uint32_t T[W];
+#pragma unroll
+      for (int q = 0; q < W; q++) T[q] = (q < w) ? 0u : (S[q] & rv[q]);
+#pragma unroll
+      for (int q = w; q < W; q++) {
+        uint32_t y = T[q];
+        while (y) {
+          const int b = __ffs(y) - 1;
+          y &= y - 1;
+          const uint32_t* rw = rows + (size_t)((q << 5) + b) * W;
+#pragma unroll
+          for (int q2 = q; q2 < W; q2++) acc += __popc(T[q2] & rw[q2]);
+        }
+      }
+    }
+  }
+  return acc;
+}
+
+struct Acc {
+  unsigned long long cnt = 0, sum = 0;
+  unsigned long long pruned = 0, words = 0, hits = 0, ins = 0, full = 0, frames = 0, heavy = 0, tasks = 0;
+};
+
+// Steps 1 and 2 for root u: bitmap rows, Algorithm 5, masks.  Returns false
+// when the soft-embedding test drops the root.
+template <int W>
+__device__ bool build_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, int d, Acc& acc) {
+  const uint32_t lane = lane_id();
+  const uint32_t k = a.k, need = k - 1;
+  const uint64_t ob = a.orow[u];
+  for (int i = lane; i < d; i += 32) st.nbr[i] = a.ocol[ob + i];
+  for (int i = lane; i < d * W; i += 32) st.rows[i] = 0u;
+  __syncwarp();
+  const uint32_t last = st.nbr[d - 1];
+  uint32_t words = 0;
+  for (int i = 0; i < d - 1; i++) {
+    const uint32_t v = st.nbr[i];
+    const uint64_t b = a.orow[v], e = a.orow[v + 1];
+    for (uint64_t p0 = b; p0 < e; p0 += 32) {
+      uint64_t p = p0 + lane;
+      uint32_t w = p < e ? a.ocol[p] : 0xFFFFFFFFu;
+      words += (p < e);
+      if (w <= last) {
+        int lo = i + 1, hi = d;  // search nbr[i+1 .. d)
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (st.nbr[mid] < w) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo < d && st.nbr[lo] == w) atomicOr(&st.rows[(size_t)i * W + (lo >> 5)], 1u << (lo & 31));
+      }
+      if (__all_sync(0xFFFFFFFFu, w > last)) break;
+    }
+  }
+  acc.words += words;
+  __syncwarp();
+  // Algorithm 5 on G[N(u) ∪ {u}], r capped at k
+  const uint32_t rcap = k;
+  if (a.prune) {
+    uint32_t root_r = rcap;
+    if (lane == 0) {
+      for (int i = d - 1; i >= 0; i--) {
+        uint32_t c = 1;
+        const uint32_t* row = st.rows + (size_t)i * W;
+        for (int w = W - 1; w >= 0 && c < rcap; w--) {
+          uint32_t x = row[w];
+          while (x && c < rcap) {
+            int b = 31 - __clz(x);
+            x &= ~(1u << b);
+            if (c <= st.rr[(w << 5) + b]) c++;
+          }
+        }
+        st.rr[i] = (uint8_t)c;
+      }
+      uint32_t c = 1;
+      for (int j = d - 1; j >= 0 && c < rcap; j--)
+        if (c <= st.rr[j]) c++;
+      root_r = c;
+    }
+    root_r = __shfl_sync(0xFFFFFFFFu, root_r, 0);
+    __syncwarp();
+    if (root_r < k) {
+      acc.pruned++;
+      return false;
+    }
+  } else {
+    for (int i = lane; i < d; i += 32) st.rr[i] = (uint8_t)rcap;
+    __syncwarp();
+  }
+  // masks[l] = local vertices with r >= l, for l in [1, k-1]
+  for (uint32_t l = 1; l <= need; l++) {
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+      int i = (w << 5) + lane;
+      bool b = i < d && st.rr[i] >= l;
+      uint32_t m = __ballot_sync(0xFFFFFFFFu, b);
+      if (lane == 0) st.masks[l * W + w] = m;
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
+template <int W>
+__device__ __forceinline__ void all_bits(int d, uint32_t (&S)[W]) {
+#pragma unroll
+  for (int w = 0; w < W; w++) {
+    int lo = w << 5;
+    S[w] = d >= lo + 32 ? 0xFFFFFFFFu : (d <= lo ? 0u : (0xFFFFFFFFu >> (lo + 32 - d)));
+  }
+}
+
+// Count of the cl-cliques of G[c] for cl <= 3, summed over the warp.
+template <int W>
+__device__ __forceinline__ unsigned long long small_count(const WarpState<W>& st, const uint32_t (&c)[W], uint32_t cl) {
+  if (cl == 1) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) s += __popc(c[w]);
+    return s;
+  }
+  if (cl == 2) return warp_sum(edges_partial<W>(c, st.rows));
+  return warp_sum(tri_partial<W>(c, st.rows, st.masks + 3 * W));
+}
+
+// Open a memoised frame for (c, cl): a stored whole key is a retrieval (returns
+// true, value in *start_sum); otherwise *start_sum/*start_pos resume after the
+// longest stored prefix of c (Sec. IV: the sibling link first, else a binary
+// search over prefix lengths).
+template <int W>
+__device__ bool memo_open(const Memo& memo, const uint32_t (&c)[W], uint32_t cl, unsigned long long* start_sum,
+                          int* start_pos, Acc& acc) {
+  unsigned long long v;
+  if (memo_find<W>(memo, c, cl, &v)) {
+    *start_sum = v;
+    acc.hits++;
+    return true;
+  }
+  int m = 0;
+#pragma unroll
+  for (int w = 0; w < W; w++) m += __popc(c[w]);
+  const int pmin = select_bit<W>(c, 0);
+  uint32_t T1[W];
+  suffix_of<W>(c, pmin + 1, T1);
+  unsigned long long hv = 0;
+  int hi = m;
+  if (m > 1 && memo_find<W>(memo, T1, cl, &hv)) {
+    hi = 1;
+  } else {
+    int lo = 2;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      uint32_t T[W];
+      suffix_of<W>(c, select_bit<W>(c, mid), T);
+      unsigned long long tv;
+      if (memo_find<W>(memo, T, cl, &tv)) {
+        hi = mid;
+        hv = tv;
+      } else {
+        lo = mid + 1;
+      }
+    }
+  }
+  *start_sum = 0;
+  *start_pos = top_bit<W>(c);
+  if (hi < m) {
+    *start_sum = hv;
+    *start_pos = select_bit<W>(c, hi) - 1;
+    acc.hits++;
+  }
+  acc.frames++;
+  return false;
+}
+
+// Eq. (1) for a candidate set c needing cl-cliques: 2 cl |E| > (cl - 1) |V|^2.
+template <int W>
+__device__ __forceinline__ bool eq1_dense(const WarpState<W>& st, const uint32_t (&c)[W], uint32_t cl, uint32_t sz) {
+  uint32_t e = warp_sum(edges_partial<W>(c, st.rows));
+  return 2ull * cl * e > (unsigned long long)(cl - 1) * sz * sz;
+}
+
+// Plain depth-first search (MODE 0 count, MODE 1 list) below the frame at
+// depth `base`, which the caller has set up (cand, pos and, for listing, the
+// sorted prefix sid of length base + 1).
+template <int W, int MODE>
+__device__ void dfs_plain(WarpState<W>& st, const EnumKArgs& a, int base, Acc& acc) {
+  const uint32_t lane = lane_id();
+  const uint32_t k = a.k, need = k - 1;
+  int depth = base;
+  while (depth >= base) {
+    const uint32_t l = need - depth;  // vertices still to pick from cand[depth]
+    const uint32_t* S = st.cand + depth * W;
+    if (MODE == 0 && l <= 3) {
+      uint32_t s[W];
+#pragma unroll
+      for (int w = 0; w < W; w++) s[w] = S[w];
+      if (l == 3) acc.cnt += tri_partial<W>(s, st.rows, st.masks + 3 * W);
+      else if (l == 2) acc.cnt += edges_partial<W>(s, st.rows);
+      else if (lane == 0) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < W; w++) c += __popc(s[w]);
+        acc.cnt += c;
+      }
+      __syncwarp();
+      depth--;
+      continue;
+    }
+    if (MODE == 1 && l == 1) {
+      // emit C ∪ {x} for each x in S: ids sorted, hashed, written
+      const int plen = depth + 1;  // root + picks
+#pragma unroll 1
+      for (int w = 0; w < W; w++) {
+        uint32_t x = S[w];
+        if (!x) continue;
+        bool mine = (x >> lane) & 1u;
+        unsigned long long base_slot = 0;
+        if (lane == 0) base_slot = atomicAdd(&a.acc[kAccWritten], (unsigned long long)__popc(x));
+        base_slot = __shfl_sync(0xFFFFFFFFu, base_slot, 0);
+        if (mine) {
+          uint32_t id = a.vert[st.nbr[(w << 5) + lane]];
+          unsigned long long slot = base_slot + __popc(x & lanemask_lt());
+          bool wr = slot < a.cap;
+          uint32_t* o = a.out + slot * (unsigned long long)k;
+          uint64_t h = mix64(0x9E3779B97F4A7C15ull ^ (uint64_t)k);
+          int j = 0;
+          bool placed = false;
+          for (int q = 0; q < plen; q++) {
+            uint32_t y = st.sid[q];
+            if (!placed && id < y) {
+              h = mix64(h ^ (uint64_t)id);
+              if (wr) o[j] = id;
+              j++;
+              placed = true;
+            }
+            h = mix64(h ^ (uint64_t)y);
+            if (wr) o[j] = y;
+            j++;
+          }
+          if (!placed) {
+            h = mix64(h ^ (uint64_t)id);
+            if (wr) o[j] = id;
+          }
+          acc.sum += h;
+          acc.cnt += 1;
+        }
+      }
+      __syncwarp();
+      depth--;
+      if (depth >= base) {
+        if (lane == 0) {
+          int plen2 = depth + 2;
+          for (int q = st.sins[depth]; q + 1 < plen2; q++) st.sid[q] = st.sid[q + 1];
+        }
+        __syncwarp();
+      }
+      continue;
+    }
+    int v = next_desc<W>(S, st.masks + l * W, st.pos[depth]);
+    if (v < 0) {
+      __syncwarp();
+      depth--;
+      if (MODE == 1 && depth >= base) {
+        if (lane == 0) {
+          int plen2 = depth + 2;
+          for (int q = st.sins[depth]; q + 1 < plen2; q++) st.sid[q] = st.sid[q + 1];
+        }
+        __syncwarp();
+      }
+      continue;
+    }
+    uint32_t c[W];
+    uint32_t sz = 0, anym = 0;
+    const uint32_t* rv = st.rows + (size_t)v * W;
+    const uint32_t* mk = st.masks + (l - 1) * W;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+      c[w] = S[w] & rv[w];
+      sz += __popc(c[w]);
+      anym |= c[w] & mk[w];
+    }
+    __syncwarp();
+    if (lane == 0) st.pos[depth] = v - 1;
+    if (sz >= l - 1 && anym) {
+      if (lane < W) st.cand[(depth + 1) * W + lane] = word_at<W>(c, lane);
+      if (lane == 0) {
+        st.pos[depth + 1] = top_bit<W>(c);
+        if (MODE == 1) {
+          uint32_t id = a.vert[st.nbr[v]];
+          int plen = depth + 1;
+          int q = plen;
+          while (q > 0 && st.sid[q - 1] > id) {
+            st.sid[q] = st.sid[q - 1];
+            q--;
+          }
+          st.sid[q] = id;
+          st.sins[depth] = (uint8_t)q;
+        }
+      }
+      depth++;
+    }
+    __syncwarp();
+  }
+}
+
+// Memoised count below the frame at depth `base` (set up by the caller: cand,
+// pos, sum, dense, fullins); returns that frame's value, the same on every lane.
+template <int W>
+__device__ unsigned long long dfs_memo(WarpState<W>& st, const EnumKArgs& a, const Memo& memo, int base, Acc& acc) {
+  const uint32_t lane = lane_id();
+  const uint32_t need = a.k - 1;
+  int depth = base;
+  unsigned long long result = 0;
+  while (true) {
+    const uint32_t l = need - depth;
+    uint32_t S[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) S[w] = st.cand[depth * W + w];
+    const bool fd = st.dense[depth];
+    int v = next_desc<W>(st.cand + depth * W, st.masks + l * W, st.pos[depth]);
+    if (v < 0) {
+      unsigned long long val = st.sum[depth];
+      if (fd && !st.fullins[depth]) {
+        int okk = memo_store<W>(memo, S, l, val);
+        acc.ins += okk;
+        acc.full += 1 - okk;
+      }
+      if (depth == base) {
+        result = val;
+        break;
+      }
+      depth--;
+      const uint32_t lp = need - depth;
+      uint32_t P[W];
+#pragma unroll
+      for (int w = 0; w < W; w++) P[w] = st.cand[depth * W + w];
+      unsigned long long ps = st.sum[depth] + val;
+      const int pv = st.cur[depth];
+      const bool pd = st.dense[depth];
+      __syncwarp();
+      if (lane == 0) st.sum[depth] = ps;
+      if (pd) {
+        uint32_t T[W];
+        suffix_of<W>(P, pv, T);
+        int okk = memo_store<W>(memo, T, lp, ps);
+        acc.ins += okk;
+        acc.full += 1 - okk;
+        bool whole = true;
+#pragma unroll
+        for (int w = 0; w < W; w++) whole &= (T[w] == P[w]);
+        if (lane == 0 && whole) st.fullins[depth] = 1;
+      }
+      __syncwarp();
+      continue;
+    }
+    __syncwarp();
+    if (lane == 0) st.pos[depth] = v - 1;
+    uint32_t c[W];
+    uint32_t sz = 0;
+    const uint32_t* rv = st.rows + (size_t)v * W;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+      c[w] = S[w] & rv[w];
+      sz += __popc(c[w]);
+    }
+    const uint32_t cl = l - 1;
+    unsigned long long val = 0;
+    bool resolved = true;
+    bool cd = false;
+    unsigned long long start_sum = 0;
+    int start_pos = -1;
+    if (cl <= 3) {
+      val = sz >= cl ? small_count<W>(st, c, cl) : 0ull;
+    } else {
+      uint32_t anym = 0;
+      const uint32_t* mk = st.masks + cl * W;
+#pragma unroll
+      for (int w = 0; w < W; w++) anym |= c[w] & mk[w];
+      if (sz >= cl && anym) {
+        cd = fd || (a.memo && eq1_dense<W>(st, c, cl, sz));
+        if (cd) {
+          if (memo_open<W>(memo, c, cl, &start_sum, &start_pos, acc)) val = start_sum;
+          else resolved = false;
+        } else {
+          resolved = false;
+          start_pos = top_bit<W>(c);
+        }
+      }
+    }
+    if (resolved) {
+      unsigned long long ns = st.sum[depth] + val;
+      __syncwarp();
+      if (lane == 0) st.sum[depth] = ns;
+      if (fd) {
+        uint32_t T[W];
+        suffix_of<W>(S, v, T);
+        int okk = memo_store<W>(memo, T, l, ns);
+        acc.ins += okk;
+        acc.full += 1 - okk;
+        bool whole = true;
+#pragma unroll
+        for (int w = 0; w < W; w++) whole &= (T[w] == S[w]);
+        if (lane == 0 && whole) st.fullins[depth] = 1;
+      }
+      __syncwarp();
+      continue;
+    }
+    // open the child frame
+    if (lane < W) st.cand[(depth + 1) * W + lane] = word_at<W>(c, lane);
+    if (lane == 0) {
+      st.cur[depth] = v;
+      st.pos[depth + 1] = start_pos;
+      st.sum[depth + 1] = cd ? start_sum : 0ull;
+      st.dense[depth + 1] = cd;
+      st.fullins[depth + 1] = 0;
+    }
+    __syncwarp();
+    depth++;
+  }
+  return result;
+}
+
+// Everything below one first-level branch v1 of a built root (a task of the
+// split path, or a branch kept local): the (k-2)-cliques of G_u ∩ N(v1).
+template <int W, int MODE>
+__device__ void run_branch(WarpState<W>& st, const EnumKArgs& a, const Memo& memo, uint32_t u, int d, int v1,
+                           Acc& acc) {
+  const uint32_t lane = lane_id();
+  const uint32_t need = a.k - 1;
+  uint32_t S0[W], c[W];
+  all_bits<W>(d, S0);
+  uint32_t sz = 0;
+  const uint32_t* rv = st.rows + (size_t)v1 * W;
+#pragma unroll
+  for (int w = 0; w < W; w++) {
+    c[w] = S0[w] & rv[w];
+    sz += __popc(c[w]);
+  }
+  const uint32_t cl = need - 1;
+  if (sz < cl) return;
+  if (MODE != 1 && cl <= 3) {
+    unsigned long long v = small_count<W>(st, c, cl);
+    if (lane == 0) acc.cnt += v;
+    return;
+  }
+  if (lane < W) st.cand[W + lane] = word_at<W>(c, lane);
+  if (MODE == 1) {
+    if (lane == 0) {
+      uint32_t iu = a.vert[u], iv = a.vert[st.nbr[v1]];
+      st.sid[0] = min(iu, iv);
+      st.sid[1] = max(iu, iv);
+      st.pos[1] = top_bit<W>(c);
+    }
+    __syncwarp();
+    dfs_plain<W, 1>(st, a, 1, acc);
+    return;
+  }
+  if (MODE == 0) {
+    if (lane == 0) st.pos[1] = top_bit<W>(c);
+    __syncwarp();
+    dfs_plain<W, 0>(st, a, 1, acc);
+    return;
+  }
+  // MODE 2
+  bool cd = a.memo && eq1_dense<W>(st, c, cl, sz);
+  unsigned long long ssum = 0;
+  int spos = top_bit<W>(c);
+  if (cd && memo_open<W>(memo, c, cl, &ssum, &spos, acc)) {
+    if (lane == 0) acc.cnt += ssum;
+    return;
+  }
+  if (lane == 0) {
+    st.pos[1] = spos;
+    st.sum[1] = cd ? ssum : 0ull;
+    st.dense[1] = cd;
+    st.fullins[1] = 0;
+  }
+  __syncwarp();
+  unsigned long long v = dfs_memo<W>(st, a, memo, 1, acc);
+  if (lane == 0) acc.cnt += v;
+}
+
+// Heavy root: copy its built state to the arena and queue one task per
+// first-level branch.  Returns false when the arena is full (keep it local).
+template <int W, int MODE>
+__device__ bool publish_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, int d, Acc& acc) {
+  const uint32_t lane = lane_id();
+  const uint32_t need = a.k - 1;
+  const uint64_t units = (16 + (uint64_t)d * 4 + (uint64_t)d * W * 4 + (uint64_t)d + 15) / 16;
+  unsigned long long off = 0;
+  if (lane == 0) off = atomicAdd(a.arena_used, units);
+  off = __shfl_sync(0xFFFFFFFFu, off, 0);
+  if (off + units > a.arena_units) return false;
+  uint8_t* base = a.arena + off * 16;
+  uint32_t* hdr = (uint32_t*)base;
+  uint32_t* nbr = hdr + 4;
+  uint32_t* rows = nbr + d;
+  uint8_t* rr = (uint8_t*)(rows + (size_t)d * W);
+  if (lane == 0) {
+    hdr[0] = u;
+    hdr[1] = (uint32_t)d;
+  }
+  for (int i = lane; i < d; i += 32) {
+    nbr[i] = st.nbr[i];
+    rr[i] = st.rr[i];
+  }
+  for (int i = lane; i < d * W; i += 32) rows[i] = st.rows[i];
+  // one task per v1 with r_v1 >= k-1
+  uint32_t S0[W];
+  all_bits<W>(d, S0);
+  const uint32_t* mk = st.masks + need * W;
+  uint32_t nt = 0;
+#pragma unroll
+  for (int w = 0; w < W; w++) nt += __popc(S0[w] & mk[w]);
+  unsigned long long t0 = 0;
+  if (lane == 0) t0 = atomicAdd(a.task_used, (unsigned long long)nt);
+  t0 = __shfl_sync(0xFFFFFFFFu, t0, 0);
+  uint32_t done = 0;
+#pragma unroll 1
+  for (int w = 0; w < W; w++) {
+    uint32_t x = S0[w] & mk[w];
+    if ((x >> lane) & 1u) {
+      unsigned long long slot = t0 + done + __popc(x & lanemask_lt());
+      if (slot < a.task_cap) a.tasks[slot] = (off << 32) | (unsigned long long)((w << 5) + lane);
+    }
+    done += __popc(x);
+  }
+  __threadfence();
+  acc.heavy++;
+  acc.tasks += nt;
+  // branches past the queue's capacity stay with this warp
+  if (t0 + nt > a.task_cap) {
+    Memo none{};
+    uint32_t skip = t0 < a.task_cap ? (uint32_t)(a.task_cap - t0) : 0u;
+    uint32_t idx = 0;
+    for (int w = 0; w < W; w++) {
+      uint32_t x = S0[w] & mk[w];
+      while (x) {
+        int b = __ffs(x) - 1;
+        x &= x - 1;
+        if (idx++ >= skip) run_branch<W, MODE == 1 ? 1 : 0>(st, a, none, u, d, (w << 5) + b, acc);
+      }
+    }
+  }
+  return true;
+}
+
+template <int W>
+__device__ void flush_acc(const EnumKArgs& a, Acc& acc) {
+  const uint32_t lane = lane_id();
+  unsigned long long cnt = warp_sum(acc.cnt);
+  unsigned long long sum = warp_sum(acc.sum);
+  unsigned long long words = warp_sum(acc.words);
+  if (lane == 0) {
+    if (cnt) atomicAdd(&a.acc[kAccCount], cnt);
+    if (sum) atomicAdd(&a.acc[kAccChecksum], sum);
+    if (acc.pruned) atomicAdd(&a.acc[kAccRootsPruned], acc.pruned);
+    if (words) atomicAdd(&a.acc[kAccBuildWords], words);
+    if (acc.hits) atomicAdd(&a.acc[kAccMemoHits], acc.hits);
+    if (acc.ins) atomicAdd(&a.acc[kAccMemoInserts], acc.ins);
+    if (acc.full) atomicAdd(&a.acc[kAccMemoFull], acc.full);
+    if (acc.frames) atomicAdd(&a.acc[kAccMemoFrames], acc.frames);
+    if (acc.heavy) atomicAdd(&a.acc[kAccRootsHeavy], acc.heavy);
+    if (acc.tasks) atomicAdd(&a.acc[kAccTasks], acc.tasks);
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void carve_state(WarpState<W>& st, const EnumKArgs& a, uint8_t* smem) {
+  const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (a.gstate) st.carve(a.gstate + gwarp * a.gstride);
+  else st.carve(smem + (size_t)(threadIdx.x >> 5) * warp_state_bytes<W>());
+}
+
+template <int W>
+__device__ __forceinline__ Memo warp_memo(const EnumKArgs& a) {
+  const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  Memo m{};
+  if (a.memo_cap) {
+    m.tags = a.memo_tags + gwarp * a.memo_cap;
+    m.keys = a.memo_keys + gwarp * a.memo_cap * W;
+    m.vals = a.memo_vals + gwarp * a.memo_cap;
+    m.cap = a.memo_cap;
+  }
+  return m;
+}
+
+__device__ __forceinline__ void next_epoch(Memo& memo, uint32_t* epoch) {
+  if (++*epoch >= (1u << 25)) {
+    for (uint32_t i = lane_id(); i < memo.cap; i += 32) memo.tags[i] = 0u;
+    __syncwarp();
+    *epoch = 1;
+  }
+  memo.tagbase = *epoch << 7;
+}
+
+// Phase 1: one warp per root, roots taken from the tier's list.
 // MODE 0: count (plain), 1: list, 2: count with memo.
 template <int W, int MODE>
 __global__ void __launch_bounds__(256) k_enum(EnumKArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = lane_id();
-  const uint32_t wib = threadIdx.x >> 5;
-  const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   WarpState<W> st;
-  if (a.gstate) st.carve(a.gstate + gwarp * a.gstride);
-  else st.carve(smem + (size_t)wib * warp_state_bytes<W>());
-
-  const uint32_t k = a.k;
-  const uint32_t need = k - 1;  // vertices to pick inside G_u
-  unsigned long long acc_cnt = 0, acc_sum = 0;
-  unsigned long long st_pruned = 0, st_words = 0, st_hits = 0, st_ins = 0, st_full = 0;
-  Memo memo{};
+  carve_state<W>(st, a, smem);
+  const uint32_t need = a.k - 1;
+  Acc acc;
+  Memo memo = warp_memo<W>(a);
   uint32_t epoch = 0;
-  if (MODE == 2) {
-    memo.tags = a.memo_tags + gwarp * a.memo_cap;
-    memo.keys = a.memo_keys + gwarp * a.memo_cap * W;
-    memo.vals = a.memo_vals + gwarp * a.memo_cap;
-    memo.cap = a.memo_cap;
-  }
-
   while (true) {
     uint32_t qi = 0;
     if (lane == 0) qi = atomicAdd(a.qctr, 1u);
     qi = __shfl_sync(0xFFFFFFFFu, qi, 0);
     if (qi >= a.nroots) break;
     const uint32_t u = a.roots[qi];
-    const uint64_t ob = a.orow[u];
-    const int d = (int)(a.orow[u + 1] - ob);
-
-    // ---- 1. bit-matrix of G_u
-    for (int i = lane; i < d; i += 32) st.nbr[i] = a.ocol[ob + i];
-    for (int i = lane; i < d * W; i += 32) st.rows[i] = 0u;
-    __syncwarp();
-    const uint32_t last = st.nbr[d - 1];
-    uint32_t words = 0;
-    for (int i = 0; i < d - 1; i++) {
-      const uint32_t v = st.nbr[i];
-      const uint64_t b = a.orow[v], e = a.orow[v + 1];
-      for (uint64_t p0 = b; p0 < e; p0 += 32) {
-        uint64_t p = p0 + lane;
-        uint32_t w = p < e ? a.ocol[p] : 0xFFFFFFFFu;
-        words += (p < e);
-        if (w <= last) {
-          int lo = i + 1, hi = d;  // search nbr[i+1 .. d)
-          while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (st.nbr[mid] < w) lo = mid + 1;
-            else hi = mid;
-          }
-          if (lo < d && st.nbr[lo] == w) atomicOr(&st.rows[(size_t)i * W + (lo >> 5)], 1u << (lo & 31));
-        }
-        if (__all_sync(0xFFFFFFFFu, w > last)) break;
-      }
-    }
-    st_words += words;
-    __syncwarp();
-
-    // ---- 2. Algorithm 5 on G[N(u) ∪ {u}], r capped at k
-    const uint32_t rcap = k;
-    uint32_t root_r = rcap;
-    if (a.prune) {
-      if (lane == 0) {
-        for (int i = d - 1; i >= 0; i--) {
-          uint32_t c = 1;
-          const uint32_t* row = st.rows + (size_t)i * W;
-          for (int w = W - 1; w >= 0 && c < rcap; w--) {
-            uint32_t x = row[w];
-            while (x && c < rcap) {
-              int b = 31 - __clz(x);
-              x &= ~(1u << b);
-              if (c <= st.rr[(w << 5) + b]) c++;
-            }
-          }
-          st.rr[i] = (uint8_t)c;
-        }
-        uint32_t c = 1;
-        for (int j = d - 1; j >= 0 && c < rcap; j--)
-          if (c <= st.rr[j]) c++;
-        root_r = c;
-      }
-      root_r = __shfl_sync(0xFFFFFFFFu, root_r, 0);
-      __syncwarp();
-      if (root_r < k) {
-        st_pruned++;
-        continue;
-      }
-    } else {
-      for (int i = lane; i < d; i += 32) st.rr[i] = (uint8_t)rcap;
-      __syncwarp();
-    }
-    // masks[l] = local vertices with r >= l, for l in [1, k-1]
-    for (uint32_t l = 1; l <= need; l++) {
-#pragma unroll
-      for (int w = 0; w < W; w++) {
-        int i = (w << 5) + lane;
-        bool b = i < d && st.rr[i] >= l;
-        uint32_t m = __ballot_sync(0xFFFFFFFFu, b);
-        if (lane == 0) st.masks[l * W + w] = m;
-      }
-    }
-    __syncwarp();
-
-    // ---- 3. search
+    const int d = (int)(a.orow[u + 1] - a.orow[u]);
+    if (!build_root<W>(st, a, u, d, acc)) continue;
     uint32_t S0[W];
-#pragma unroll
-    for (int w = 0; w < W; w++) {
-      int lo = w << 5;
-      S0[w] = d >= lo + 32 ? 0xFFFFFFFFu : (d <= lo ? 0u : (0xFFFFFFFFu >> (lo + 32 - d)));
+    all_bits<W>(d, S0);
+    if (MODE == 2) next_epoch(memo, &epoch);
+    // Eq. (1) on G_u for the root frame
+    bool dense0 = false;
+    if (MODE == 2 && a.memo && need > 3) {
+      uint32_t er = 0;
+      for (int i = lane; i < d * W; i += 32) er += __popc(st.rows[i]);
+      er = warp_sum(er);
+      dense0 = 2ull * need * er > (unsigned long long)(need - 1) * d * d;
     }
-
+    // heavy roots go to the split path: one task per first-level branch
+    if (a.split_wedges && d > a.split_min_d && !dense0 && need >= 4) {
+      uint32_t wg = 0;
+      for (int i = lane; i < d; i += 32) {
+        uint32_t p = 0;
+#pragma unroll
+        for (int w = 0; w < W; w++) p += __popc(st.rows[(size_t)i * W + w]);
+        wg += p * (p - 1) / 2;
+      }
+      wg = warp_sum(wg);
+      if (wg > a.split_wedges && publish_root<W, MODE>(st, a, u, d, acc)) continue;
+    }
     if (MODE == 0 || MODE == 1) {
-      // plain depth-first search
       if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
       if (lane == 0) {
         st.pos[0] = d - 1;
         st.sid[0] = a.vert[u];
       }
       __syncwarp();
-      int depth = 0;
-      while (depth >= 0) {
-        const uint32_t l = need - depth;  // vertices still to pick from cand[depth]
-        const uint32_t* S = st.cand + depth * W;
-        if (MODE == 0 && l == 2) {
-          uint32_t s[W];
-#pragma unroll
-          for (int w = 0; w < W; w++) s[w] = S[w];
-          acc_cnt += edges_partial<W>(s, st.rows);
-          depth--;
-          continue;
-        }
-        if (l == 1) {
-          if (MODE == 0) {
-            uint32_t c = 0;
-#pragma unroll
-            for (int w = 0; w < W; w++) c += __popc(S[w]);
-            if (lane == 0) acc_cnt += c;
-          } else {
-            // emit C ∪ {x} for each x in S: ids sorted, hashed, written
-            const int plen = depth + 1;  // root + picks
-#pragma unroll 1
-            for (int w = 0; w < W; w++) {
-              uint32_t x = S[w];
-              if (!x) continue;
-              bool mine = (x >> lane) & 1u;
-              unsigned long long base = 0;
-              if (lane == 0) base = atomicAdd(&a.acc[kAccWritten], (unsigned long long)__popc(x));
-              base = __shfl_sync(0xFFFFFFFFu, base, 0);
-              if (mine) {
-                uint32_t id = a.vert[st.nbr[(w << 5) + lane]];
-                unsigned long long slot = base + __popc(x & lanemask_lt());
-                bool wr = slot < a.cap;
-                uint32_t* o = a.out + slot * (unsigned long long)k;
-                uint64_t h = mix64(0x9E3779B97F4A7C15ull ^ (uint64_t)k);
-                int j = 0;
-                bool placed = false;
-                for (int q = 0; q < plen; q++) {
-                  uint32_t y = st.sid[q];
-                  if (!placed && id < y) {
-                    h = mix64(h ^ (uint64_t)id);
-                    if (wr) o[j] = id;
-                    j++;
-                    placed = true;
-                  }
-                  h = mix64(h ^ (uint64_t)y);
-                  if (wr) o[j] = y;
-                  j++;
-                }
-                if (!placed) {
-                  h = mix64(h ^ (uint64_t)id);
-                  if (wr) o[j] = id;
-                }
-                acc_sum += h;
-                acc_cnt += 1;
-              }
-            }
-          }
-          depth--;
-          if (MODE == 1 && depth >= 0) {
-            // remove the pick of `depth` from the sorted prefix
-            __syncwarp();
-            if (lane == 0) {
-              int plen = depth + 2;
-              for (int q = st.sins[depth]; q + 1 < plen; q++) st.sid[q] = st.sid[q + 1];
-            }
-            __syncwarp();
-          }
-          continue;
-        }
-        int v = next_desc<W>(S, st.masks + l * W, st.pos[depth]);
-        if (v < 0) {
-          depth--;
-          if (MODE == 1 && depth >= 0) {
-            __syncwarp();
-            if (lane == 0) {
-              int plen = depth + 2;
-              for (int q = st.sins[depth]; q + 1 < plen; q++) st.sid[q] = st.sid[q + 1];
-            }
-            __syncwarp();
-          }
-          continue;
-        }
-        uint32_t c[W];
-        uint32_t sz = 0, anym = 0;
-        const uint32_t* rv = st.rows + (size_t)v * W;
-        const uint32_t* mk = st.masks + (l - 1) * W;
-#pragma unroll
-        for (int w = 0; w < W; w++) {
-          c[w] = S[w] & rv[w];
-          sz += __popc(c[w]);
-          anym |= c[w] & mk[w];
-        }
-        __syncwarp();
-        if (lane == 0) st.pos[depth] = v - 1;
-        if (sz >= l - 1 && anym) {
-          if (lane < W) st.cand[(depth + 1) * W + lane] = word_at<W>(c, lane);
-          if (lane == 0) {
-            st.pos[depth + 1] = top_bit<W>(c);
-            if (MODE == 1) {
-              // insert the pick's id into the sorted prefix
-              uint32_t id = a.vert[st.nbr[v]];
-              int plen = depth + 1;
-              int q = plen;
-              while (q > 0 && st.sid[q - 1] > id) {
-                st.sid[q] = st.sid[q - 1];
-                q--;
-              }
-              st.sid[q] = id;
-              st.sins[depth] = (uint8_t)q;
-            }
-          }
-          depth++;
-        }
-        __syncwarp();
-      }
+      dfs_plain<W, MODE>(st, a, 0, acc);
     } else {
-      // ---- memoised count (device form of the Induced Subgraph Trie)
-      if (++epoch >= (1u << 25)) {
-        for (uint32_t i = lane; i < memo.cap; i += 32) memo.tags[i] = 0u;
-        __syncwarp();
-        epoch = 1;
-      }
-      memo.tagbase = epoch << 7;
-      // root frame density, Eq. (1): 2 l |E| > (l - 1) |V|^2 with l = k - 1
-      uint32_t er = 0;
-      for (int i = lane; i < d * W; i += 32) er += __popc(st.rows[i]);
-      er = warp_sum(er);
-      const uint32_t l0 = need;
-      bool dense0 = a.memo && l0 > 3 && 2ull * l0 * er > (unsigned long long)(l0 - 1) * d * d;
-      if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
-      if (lane == 0) {
-        st.pos[0] = d - 1;
-        st.sum[0] = 0;
-        st.dense[0] = dense0;
-        st.fullins[0] = 0;
-      }
-      __syncwarp();
-      int depth = 0;
-      unsigned long long root_total = 0;
-      while (true) {
-        const uint32_t l = need - depth;
-        uint32_t S[W];
-#pragma unroll
-        for (int w = 0; w < W; w++) S[w] = st.cand[depth * W + w];
-        const bool fd = st.dense[depth];
-        int v = next_desc<W>(st.cand + depth * W, st.masks + l * W, st.pos[depth]);
-        if (v < 0) {
-          unsigned long long val = st.sum[depth];
-          if (fd && !st.fullins[depth]) {
-            int okk = memo_store<W>(memo, S, l, val);
-            st_ins += okk;
-            st_full += 1 - okk;
-          }
-          if (depth == 0) {
-            root_total = val;
-            break;
-          }
-          depth--;
-          const uint32_t lp = need - depth;
-          uint32_t P[W];
-#pragma unroll
-          for (int w = 0; w < W; w++) P[w] = st.cand[depth * W + w];
-          unsigned long long ps = st.sum[depth] + val;
-          const int pv = st.cur[depth];
-          __syncwarp();
-          if (lane == 0) st.sum[depth] = ps;
-          if (st.dense[depth]) {
-            uint32_t T[W];
-            suffix_of<W>(P, pv, T);
-            int okk = memo_store<W>(memo, T, lp, ps);
-            st_ins += okk;
-            st_full += 1 - okk;
-            // whole set stored when pv is the smallest vertex of P
-            bool whole = true;
-#pragma unroll
-            for (int w = 0; w < W; w++) whole &= (T[w] == P[w]);
-            if (lane == 0 && whole) st.fullins[depth] = 1;
-          }
-          __syncwarp();
-          continue;
-        }
-        __syncwarp();
-        if (lane == 0) st.pos[depth] = v - 1;
-        uint32_t c[W];
-        uint32_t sz = 0;
-        const uint32_t* rv = st.rows + (size_t)v * W;
-#pragma unroll
-        for (int w = 0; w < W; w++) {
-          c[w] = S[w] & rv[w];
-          sz += __popc(c[w]);
-        }
-        const uint32_t cl = l - 1;
-        unsigned long long val = 0;
-        bool resolved = true;
-        bool cd = false;
-        unsigned long long start_sum = 0;
-        int start_pos = -1;
-        if (cl == 1) {
-          val = sz;
-        } else if (cl == 2) {
-          val = warp_sum(edges_partial<W>(c, st.rows));
-        } else {
-          uint32_t anym = 0;
-          const uint32_t* mk = st.masks + cl * W;
-#pragma unroll
-          for (int w = 0; w < W; w++) anym |= c[w] & mk[w];
-          if (sz >= cl && anym) {
-            cd = fd;
-            if (!cd && a.memo && cl > 3) {
-              uint32_t e = warp_sum(edges_partial<W>(c, st.rows));
-              cd = 2ull * cl * e > (unsigned long long)(cl - 1) * sz * sz;
-            }
-            if (cd && memo_find<W>(memo, c, cl, &val)) {
-              st_hits++;
-            } else {
-              resolved = false;
-              start_pos = top_bit<W>(c);
-              if (cd) {
-                // longest stored prefix (largest-vertex side) of c at level cl:
-                // the smallest j in [1, m] whose suffix c ∩ [p_j, ∞) is stored
-                // (j = m stands for the empty suffix, count 0).
-                int m = 0;
-#pragma unroll
-                for (int w = 0; w < W; w++) m += __popc(c[w]);
-                int lo = 1, hi = m;
-                unsigned long long hv = 0;
-                while (lo < hi) {
-                  int mid = (lo + hi) >> 1;
-                  uint32_t T[W];
-                  suffix_of<W>(c, select_bit<W>(c, mid), T);
-                  unsigned long long tv;
-                  if (memo_find<W>(memo, T, cl, &tv)) {
-                    hi = mid;
-                    hv = tv;
-                  } else {
-                    lo = mid + 1;
-                  }
-                }
-                if (hi < m) {
-                  start_sum = hv;
-                  start_pos = select_bit<W>(c, hi) - 1;
-                  st_hits++;
-                }
-              }
-            }
-          }
-        }
-        if (resolved) {
-          unsigned long long ns = st.sum[depth] + val;
-          __syncwarp();
-          if (lane == 0) st.sum[depth] = ns;
-          if (fd) {
-            uint32_t T[W];
-            suffix_of<W>(S, v, T);
-            int okk = memo_store<W>(memo, T, l, ns);
-            st_ins += okk;
-            st_full += 1 - okk;
-            bool whole = true;
-#pragma unroll
-            for (int w = 0; w < W; w++) whole &= (T[w] == S[w]);
-            if (lane == 0 && whole) st.fullins[depth] = 1;
-          }
-          __syncwarp();
-          continue;
-        }
-        // open the child frame
-        if (lane < W) st.cand[(depth + 1) * W + lane] = word_at<W>(c, lane);
+      if (need <= 3) {
+        unsigned long long v = small_count<W>(st, S0, need);
+        if (lane == 0) acc.cnt += v;
+      } else {
+        if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
         if (lane == 0) {
-          st.cur[depth] = v;
-          st.pos[depth + 1] = start_pos;
-          st.sum[depth + 1] = start_sum;
-          st.dense[depth + 1] = cd;
-          st.fullins[depth + 1] = 0;
+          st.pos[0] = d - 1;
+          st.sum[0] = 0;
+          st.dense[0] = dense0;
+          st.fullins[0] = 0;
         }
         __syncwarp();
-        depth++;
+        unsigned long long v = dfs_memo<W>(st, a, memo, 0, acc);
+        if (lane == 0) acc.cnt += v;
       }
-      if (lane == 0) acc_cnt += root_total;
     }
     __syncwarp();
   }
-  // ---- reduce this warp's partials
-  acc_cnt = warp_sum(acc_cnt);
-  acc_sum = warp_sum(acc_sum);
-  st_words = warp_sum(st_words);
-  if (lane == 0) {
-    if (acc_cnt) atomicAdd(&a.acc[kAccCount], acc_cnt);
-    if (acc_sum) atomicAdd(&a.acc[kAccChecksum], acc_sum);
-    if (st_pruned) atomicAdd(&a.acc[kAccRootsPruned], st_pruned);
-    if (st_words) atomicAdd(&a.acc[kAccBuildWords], st_words);
-    if (st_hits) atomicAdd(&a.acc[kAccMemoHits], st_hits);
-    if (st_ins) atomicAdd(&a.acc[kAccMemoInserts], st_ins);
-    if (st_full) atomicAdd(&a.acc[kAccMemoFull], st_full);
+  flush_acc<W>(a, acc);
+}
+
+// Phase 2: the split path.  Every warp takes (root, v1) tasks; a root's built
+// state is loaded from the arena when the task's root changes.
+template <int W, int MODE>
+__global__ void __launch_bounds__(256) k_tasks(EnumKArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t lane = lane_id();
+  WarpState<W> st;
+  carve_state<W>(st, a, smem);
+  const uint32_t need = a.k - 1;
+  Acc acc;
+  Memo memo = warp_memo<W>(a);
+  uint32_t epoch = 1u << 24;  // above every epoch of phase 1
+  const unsigned long long ntasks = min(*(volatile unsigned long long*)a.task_used, a.task_cap);
+  unsigned long long cur = ~0ull;
+  uint32_t u = 0;
+  int d = 0;
+  while (true) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(a.task_head, 1ull);
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    if (t >= ntasks) break;
+    const unsigned long long task = a.tasks[t];
+    const unsigned long long off = task >> 32;
+    const int v1 = (int)(task & 0xFFFFFFFFull);
+    if (off != cur) {
+      const uint8_t* base = a.arena + off * 16;
+      const uint32_t* hdr = (const uint32_t*)base;
+      u = hdr[0];
+      d = (int)hdr[1];
+      const uint32_t* nbr = hdr + 4;
+      const uint32_t* rows = nbr + d;
+      const uint8_t* rr = (const uint8_t*)(rows + (size_t)d * W);
+      for (int i = lane; i < d; i += 32) {
+        st.nbr[i] = nbr[i];
+        st.rr[i] = rr[i];
+      }
+      for (int i = lane; i < d * W; i += 32) st.rows[i] = rows[i];
+      __syncwarp();
+      for (uint32_t l = 1; l <= need; l++) {
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+          int i = (w << 5) + lane;
+          bool b = i < d && st.rr[i] >= l;
+          uint32_t m = __ballot_sync(0xFFFFFFFFu, b);
+          if (lane == 0) st.masks[l * W + w] = m;
+        }
+      }
+      __syncwarp();
+      cur = off;
+      if (MODE == 2) next_epoch(memo, &epoch);
+    }
+    run_branch<W, MODE>(st, a, memo, u, d, v1, acc);
+    __syncwarp();
   }
+  flush_acc<W>(a, acc);
 }
 
 // k = 1 listing: every vertex of the rank range is a clique.
@@ -718,28 +1046,46 @@ struct TierPlan {
   uint64_t gstate_bytes = 0;   // per-warp state in global memory (0: in shared memory)
   uint32_t memo_cap = 0;       // entries per warp (0: no memo)
   uint64_t memo_bytes = 0;
+  bool split = false;          // heavy roots of this tier go to the split path
+  uint64_t arena_units = 0;    // 16-byte units for published roots
+  uint64_t task_cap = 0;       // (root, branch) task slots
   const void* fn = nullptr;
+  const void* fn_tasks = nullptr;
 };
 
+// Bytes of one published root of width W: header, out-neighbours, bit-matrix rows, r values.
+__host__ __device__ constexpr uint64_t published_root_units(int W) {
+  return (16 + 32ull * W * 4 + 32ull * W * W * 4 + 32ull * W + 15) / 16;
+}
+
 template <int W, int MODE>
-static int plan_tier(kc_ctx* ctx, uint32_t nroots, TierPlan* tp) {
+static int plan_tier(kc_ctx* ctx, uint32_t nroots, bool split, TierPlan* tp) {
   constexpr size_t wbytes = warp_state_bytes<W>();
   const bool in_smem = W <= 8;
   tp->W = W;
   tp->mode = MODE;
   tp->nroots = nroots;
   tp->fn = (const void*)k_enum<W, MODE>;
+  tp->fn_tasks = (const void*)k_tasks<W, MODE>;
   if (nroots == 0) return KC_OK;
   tp->warps_per_block = W <= 4 ? 8 : 4;
   tp->smem = in_smem ? wbytes * tp->warps_per_block : 0;
-  if (tp->smem > 48 * 1024)
+  if (tp->smem > 48 * 1024) {
     KC_CUDA(cudaFuncSetAttribute(k_enum<W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp->smem));
+    KC_CUDA(cudaFuncSetAttribute(k_tasks<W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp->smem));
+  }
   int per_sm = 0;
   KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enum<W, MODE>, tp->warps_per_block * 32, tp->smem));
   per_sm = std::max(per_sm, 1);
   uint64_t blocks = (uint64_t)ctx->num_sms * per_sm;
   uint64_t need_blocks = (nroots + tp->warps_per_block - 1) / tp->warps_per_block;
-  blocks = std::max<uint64_t>(1, std::min(blocks, need_blocks));
+  // a split tier keeps the whole grid: its task phase has many more work items than roots
+  if (!split) blocks = std::max<uint64_t>(1, std::min(blocks, need_blocks));
+  tp->split = split;
+  if (split) {
+    tp->arena_units = (uint64_t)nroots * published_root_units(W);
+    tp->task_cap = std::min<uint64_t>((uint64_t)nroots * 32 * W, 1ull << 26);
+  }
   if (!in_smem) {
     uint64_t max_warps = std::max<uint64_t>(4, (1ull << 30) / wbytes);
     blocks = std::max<uint64_t>(1, std::min<uint64_t>(blocks, max_warps / tp->warps_per_block));
@@ -759,21 +1105,26 @@ static int plan_tier(kc_ctx* ctx, uint32_t nroots, TierPlan* tp) {
 }
 
 template <int MODE>
-static int plan_all(kc_ctx* ctx, const uint32_t* hcnt, TierPlan* plans) {
+static int plan_all(kc_ctx* ctx, const uint32_t* hcnt, bool split, TierPlan* plans) {
   // tiers wider than 8 words keep their state in global memory and count without the memo
   constexpr int M16 = (MODE == 2) ? 0 : MODE;
-  KC_TRY((plan_tier<1, MODE>(ctx, hcnt[0], &plans[0])));
-  KC_TRY((plan_tier<2, MODE>(ctx, hcnt[1], &plans[1])));
-  KC_TRY((plan_tier<4, MODE>(ctx, hcnt[2], &plans[2])));
-  KC_TRY((plan_tier<8, MODE>(ctx, hcnt[3], &plans[3])));
-  KC_TRY((plan_tier<16, M16>(ctx, hcnt[4], &plans[4])));
-  KC_TRY((plan_tier<32, M16>(ctx, hcnt[5], &plans[5])));
+  KC_TRY((plan_tier<1, MODE>(ctx, hcnt[0], false, &plans[0])));
+  KC_TRY((plan_tier<2, MODE>(ctx, hcnt[1], split, &plans[1])));
+  KC_TRY((plan_tier<4, MODE>(ctx, hcnt[2], split, &plans[2])));
+  KC_TRY((plan_tier<8, MODE>(ctx, hcnt[3], split, &plans[3])));
+  KC_TRY((plan_tier<16, M16>(ctx, hcnt[4], split, &plans[4])));
+  KC_TRY((plan_tier<32, M16>(ctx, hcnt[5], split, &plans[5])));
   return KC_OK;
 }
+
+// Default split test: a root of a split tier is split when the wedge count of
+// its G_u (sum over local vertices of C(out-degree, 2)) exceeds this.
+constexpr uint32_t kDefaultSplitWedges = 16384;
 
 int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s) {
   kc_stats stt{};
   uint32_t launches = 0, enum_launches = 0;
+  uint32_t tier_roots[kTiers] = {0};
   cudaEvent_t* ev = ctx->ev;
   KC_CUDA(cudaEventRecord(ev[5], s));
   KC_CUDA(cudaMemsetAsync(ctx->d_acc, 0, kAccSlots * sizeof(unsigned long long), s));
@@ -809,18 +1160,27 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
     if (hcnt[kTiers] != 0) return KC_E_UNSUPPORTED;  // out-degree above the widest tier
     // memo needs at least one level to split (k >= 3); k = 2 counts by popcount
     const int mode = ea.mode == 1 ? 1 : ((ea.memo && k >= 3) ? 2 : 0);
+    const uint32_t split_wedges =
+        ctx->opts.split_threshold == 0 ? kDefaultSplitWedges
+        : (ctx->opts.split_threshold == 0xFFFFFFFFu ? 0u : ctx->opts.split_threshold);
+    // the split path needs at least two levels below the first branch
+    const bool split = split_wedges != 0 && k >= 5;
     TierPlan plans[kTiers];
-    if (mode == 1) KC_TRY(plan_all<1>(ctx, hcnt, plans));
-    else if (mode == 2) KC_TRY(plan_all<2>(ctx, hcnt, plans));
-    else KC_TRY(plan_all<0>(ctx, hcnt, plans));
-    // one scratch region for every tier's global state and memo tables
+    if (mode == 1) KC_TRY(plan_all<1>(ctx, hcnt, split, plans));
+    else if (mode == 2) KC_TRY(plan_all<2>(ctx, hcnt, split, plans));
+    else KC_TRY(plan_all<0>(ctx, hcnt, split, plans));
+    // one scratch region for every tier's global state, memo tables, arena and task queue
     uint64_t total = 0;
-    uint64_t goff[kTiers], moff[kTiers];
+    uint64_t goff[kTiers], moff[kTiers], aoff[kTiers], toff[kTiers];
     for (int t = 0; t < kTiers; t++) {
       goff[t] = total;
       total += (plans[t].gstate_bytes * plans[t].blocks * std::max(plans[t].warps_per_block, 1) + 255) & ~255ull;
       moff[t] = total;
       total += (plans[t].memo_bytes + 255) & ~255ull;
+      aoff[t] = total;
+      total += (plans[t].arena_units * 16 + 255) & ~255ull;
+      toff[t] = total;
+      total += (plans[t].task_cap * 8 + 255) & ~255ull;
     }
     void* base = nullptr;
     if (total) KC_TRY(scratch_get(ctx, kScrEnum, total, &base));
@@ -859,14 +1219,34 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
         x.memo_cap = tp.memo_cap;
         KC_CUDA(cudaMemsetAsync(x.memo_tags, 0, warps * tp.memo_cap * 4, ts));
       }
+      if (tp.split) {
+        x.split_wedges = split_wedges;
+        x.split_min_d = 32;
+        x.arena = (uint8_t*)base + aoff[t];
+        x.arena_units = tp.arena_units;
+        x.arena_used = &ctx->d_acc[kAccArena0 + t];
+        x.tasks = (unsigned long long*)((uint8_t*)base + toff[t]);
+        x.task_cap = tp.task_cap;
+        x.task_used = &ctx->d_acc[kAccTaskUsed0 + t];
+        x.task_head = &ctx->d_acc[kAccTaskHead0 + t];
+      }
       void* kargs[] = {&x};
+      KC_CUDA(cudaEventRecord(ctx->ev_tier0[t], ts));
       KC_CUDA(cudaLaunchKernel(tp.fn, dim3((unsigned)tp.blocks), dim3(tp.warps_per_block * 32), kargs, tp.smem, ts));
       launches++;
       enum_launches++;
+      if (tp.split) {
+        // second phase: (root, first-level branch) tasks of the roots the first phase published
+        KC_CUDA(cudaLaunchKernel(tp.fn_tasks, dim3((unsigned)tp.blocks), dim3(tp.warps_per_block * 32), kargs, tp.smem,
+                                 ts));
+        launches++;
+        enum_launches++;
+      }
+      KC_CUDA(cudaEventRecord(ctx->ev_tier1[t], ts));
       KC_CUDA(cudaEventRecord(ctx->ev_join[t], ts));
       KC_CUDA(cudaStreamWaitEvent(s, ctx->ev_join[t], 0));
     }
-    for (int t = 4; t < kTiers; t++) stt.roots_heavy += hcnt[t];
+    for (int t = 0; t < kTiers; t++) tier_roots[t] = hcnt[t];
     KC_CUDA(cudaEventRecord(ev[7], s));
   }
   KC_CUDA(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc, kAccSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -883,6 +1263,15 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
   stt.memo_hits = ctx->h_acc[kAccMemoHits];
   stt.memo_inserts = ctx->h_acc[kAccMemoInserts];
   stt.memo_full = ctx->h_acc[kAccMemoFull];
+  stt.memo_frames = ctx->h_acc[kAccMemoFrames];
+  stt.roots_heavy = ctx->h_acc[kAccRootsHeavy];
+  if (k >= 2) {
+    for (int t = 0; t < kTiers; t++) {
+      stt.roots_tier[t] = tier_roots[t];
+      stt.ms_tier[t] = 0.f;
+      if (tier_roots[t]) cudaEventElapsedTime(&stt.ms_tier[t], ctx->ev_tier0[t], ctx->ev_tier1[t]);
+    }
+  }
   ctx->last = stt;
   return KC_OK;
 }

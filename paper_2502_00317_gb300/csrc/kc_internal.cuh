@@ -131,6 +131,8 @@ struct kc_ctx {
   cudaEvent_t ev[16] = {};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[kc::kTiers] = {};
+  cudaEvent_t ev_tier0[kc::kTiers] = {};
+  cudaEvent_t ev_tier1[kc::kTiers] = {};
   cudaStream_t tier_stream[kc::kTiers] = {};
   kc_stats last{};
   kc_upload_stats last_up{};
@@ -151,15 +153,19 @@ enum AccSlot : int {
   kAccMemoHits,
   kAccMemoInserts,
   kAccMemoFull,
-  kAccQueue0,      // work-queue counters (one per enumerator launch)
-  kAccQueueLast = kAccQueue0 + 15,
-  kAccSlots
+  kAccMemoFrames,
+  kAccTasks,
+  kAccQueue0,      // root-queue counters (one per width tier)
+  kAccArena0 = kAccQueue0 + kTiers,     // split path: arena units used, per tier
+  kAccTaskUsed0 = kAccArena0 + kTiers,  // split path: tasks queued, per tier
+  kAccTaskHead0 = kAccTaskUsed0 + kTiers,  // split path: tasks taken, per tier
+  kAccSlots = kAccTaskHead0 + kTiers
 };
 
 // Scratch slots.
 enum ScratchSlot : int {
   kScrA = 0, kScrB, kScrC, kScrD, kScrE, kScrF, kScrG, kScrScan, kScrSort, kScrSortList, kScrEnum, kScrMemo,
-  kScrRoots, kScrPeel,
+  kScrRoots, kScrPeel, kScrSplit,
   kScrSlots
 };
 

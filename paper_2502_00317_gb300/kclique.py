@@ -84,6 +84,9 @@ class kc_stats(ctypes.Structure):
         ("memo_hits", ctypes.c_uint64),
         ("memo_inserts", ctypes.c_uint64),
         ("memo_full", ctypes.c_uint64),
+        ("memo_frames", ctypes.c_uint64),
+        ("ms_tier", ctypes.c_float * 6),
+        ("roots_tier", ctypes.c_uint32 * 6),
     ]
 
 
@@ -99,7 +102,11 @@ class kc_upload_stats(ctypes.Structure):
 
 
 def _struct_dict(s) -> dict:
-    return {name: getattr(s, name) for name, _ in s._fields_}
+    out = {}
+    for name, _ in s._fields_:
+        v = getattr(s, name)
+        out[name] = list(v) if isinstance(v, ctypes.Array) else v
+    return out
 
 
 @lru_cache(maxsize=1)
@@ -161,8 +168,9 @@ def kc_strerror(status: int) -> str:
 
 
 def kc_create(device: int = 0, no_memo: bool = False, no_prune: bool = False, memo_bytes: int = 0,
-              spin_limit: int = 0) -> int:
-    o = kc_opts(ctypes.sizeof(kc_opts), int(no_memo), int(no_prune), 0, int(memo_bytes), int(spin_limit))
+              spin_limit: int = 0, split_threshold: int = 0) -> int:
+    o = kc_opts(ctypes.sizeof(kc_opts), int(no_memo), int(no_prune), int(split_threshold), int(memo_bytes),
+                int(spin_limit))
     h = ctypes.c_void_p()
     _check(load().kc_create(ctypes.byref(h), int(device), ctypes.byref(o)), "kc_create")
     return h.value

@@ -200,6 +200,41 @@ def test_chung_lu_small_tiers(ctx, ctx_plain, ctx_memo_only):
             c.free(h)
 
 
+@pytest.mark.parametrize("maker,splits", [
+    (lambda: gg.chung_lu_planted(n=20000, n_cliques=40, seed=1), False),  # wide roots are dense: memo, no split
+    (lambda: gg.rgg_torus(4000, 70.0, seed=6), True),
+    (lambda: gg.er_gnp(400, 0.3, 12), True),
+])
+def test_split_path_matches_oracle(maker, splits):
+    """Heavy-root split (one task per first-level branch, drained by a second
+    launch): forced on every root of the split tiers, and switched off, in
+    count mode with and without the memo and in list mode."""
+    g = maker()
+    og = oracle.OracleGraph.from_graph(g)
+    ctxs = [kc.Context(0, split_threshold=1), kc.Context(0, split_threshold=1, no_memo=True),
+            kc.Context(0, split_threshold=0xFFFFFFFF)]
+    try:
+        hs = [c.upload_host(g.n, g.rowptr, g.col) for c in ctxs]
+        heavy = 0
+        for k in (5, 6, 7, 8):
+            want = og.count(k)[0]
+            for c, h in zip(ctxs, hs):
+                assert c.count(h, k) == want, (k, c.stats())
+            heavy += ctxs[0].stats()["roots_heavy"]
+            assert ctxs[2].stats()["roots_heavy"] == 0
+        assert (heavy > 0) == splits
+        for k in (5, 6):
+            want = og.checksum(k)
+            for c, h in zip(ctxs, hs):
+                assert c.list(h, k, None, 0)[1:] == want, k
+        if og.count(5)[0] <= 300000:
+            arr, t, s = _list_all(ctxs[0], hs[0], 5, og.count(5)[0])
+            assert np.array_equal(np.unique(arr, axis=0), np.unique(og.list(5)[0], axis=0))
+    finally:
+        for c in ctxs:
+            c.close()
+
+
 # ------------------------------------------------- peel / orient (a2, a3)
 @pytest.mark.parametrize("maker", [
     lambda: gg.er_gnp(3000, 0.004, 7),

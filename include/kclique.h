@@ -173,6 +173,48 @@ int kc_list(kc_ctx* ctx, kc_graph g, uint32_t k, uint32_t* d_buf, uint64_t cap, 
 int kc_list_range(kc_ctx* ctx, kc_graph g, uint32_t k, uint32_t root_lo, uint32_t root_hi, uint32_t* d_buf,
                   uint64_t cap, uint64_t* written, uint64_t* total, uint64_t* checksum, void* stream);
 
+/*
+ * Count the k-cliques of a DAG that is already in device memory, without
+ * allocating any memory.  The paper has no counterpart: this entry point is
+ * for callers that cannot call cudaMalloc (or any allocator) when they
+ * count: a process whose own pool allocator already holds the device's free
+ * memory (a serving framework, a deep-learning runtime), where a further
+ * cudaMalloc fails or fragments that pool; a latency-bound loop that cannot
+ * afford cudaMalloc/cudaFree, which can synchronise the whole device; code
+ * that must not fail for lack of memory once it has started.  Such callers
+ * cannot create a kc_ctx either (kc_create and kc_upload allocate), so this
+ * call takes no context.
+ *
+ * Input (device memory of the current device, caller-owned, read only):
+ *   d_orow[n+1] uint64 row offsets, d_orow[0] = 0, non-decreasing;
+ *   d_ocol[d_orow[n]] uint32 out-neighbours: row r lists ranks strictly
+ *   ascending, each in (r, n) -- an oriented DAG in rank space such as
+ *   kc_export_dag returns (any total order gives the same count).
+ * Output: *count (host) = the number of k-cliques; k = 1 gives n, k = 2 the
+ * number of DAG edges.  The work is the plain count of kc_count (one warp per
+ * root, Algorithm 5 pruning) without the memo and without the heavy-root
+ * split.
+ *
+ * Scratch lives in one fixed device array of 3 MiB + 768 B inside the
+ * library, which every GPU that loads libkc.so holds until the process
+ * exits.  Its limits: every out-degree at most 256 (else KC_E_UNSUPPORTED,
+ * nothing counted); roots are binned 131,072 at a time, so n is not
+ * otherwise bounded.  The array keeps the last call's contents; each call
+ * clears what must start at zero.  All calls on a device share the one
+ * array, so calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and give wrong counts: serialise them.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Errors: KC_E_INVALID_ARG (NULL d_orow or
+ * count, NULL d_ocol with edges, k = 0), KC_E_UNSUPPORTED (k > KC_MAX_K,
+ * out-degree > 256), KC_E_INVALID_GRAPH (the DAG breaks the layout above;
+ * checked on the device before any other kernel reads it), KC_E_CUDA.
+ * Synchronises `stream` (NULL: the legacy default stream) several times.
+ */
+int kc_count_dag_noalloc(uint32_t n, const uint64_t* d_orow, const uint32_t* d_ocol, uint32_t k, uint64_t* count,
+                         void* stream);
+
 /* Telemetry of the last count/list call, and of the last upload. */
 int kc_last_stats(kc_ctx* ctx, kc_stats* out);
 int kc_last_upload_stats(kc_ctx* ctx, kc_upload_stats* out);

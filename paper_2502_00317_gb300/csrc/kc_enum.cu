@@ -26,6 +26,7 @@
 //          Eq. (1) density test decides where this starts; below a dense
 //          frame every frame is memoised, as Algorithm 3 recurses into itself.
 #include <algorithm>
+#include <mutex>
 
 #include "kc_internal.cuh"
 
@@ -1277,3 +1278,168 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
 }
 
 }  // namespace kc
+
+// ------------------------------------------- counting without allocating
+// kc_count_dag_noalloc: the plain count of k_enum (mode 0, pruning on, no
+// memo, no split) over a DAG the caller already holds on the device, with
+// all of its scratch (accumulators, root lists) in one fixed device array.
+// It exists for callers that must not allocate device memory; see the
+// declaration in kclique.h for the contract.
+namespace kc {
+namespace {
+constexpr uint32_t kStaticChunk = 1u << 17;  // roots binned per pass
+constexpr size_t kStaticAccBytes = 512;      // accumulator slots
+constexpr size_t kStaticCntBytes = 256;      // tier counts (16 words), status word
+constexpr size_t kStaticListBytes = (size_t)kTiers * kStaticChunk * sizeof(uint32_t);
+constexpr size_t kStaticBytes = kStaticAccBytes + kStaticCntBytes + kStaticListBytes;  // 3 MiB + 768 B
+static_assert(kAccSlots * sizeof(unsigned long long) <= kStaticAccBytes, "accumulators do not fit");
+constexpr int kStaticMaxDevices = 64;
+}  // namespace
+}  // namespace kc
+
+// Shared by every call on a device; held by each GPU that loads the library until the process exits.
+static __device__ __align__(256) uint8_t g_kc_static_scratch[kc::kStaticBytes];
+
+namespace kc {
+namespace {
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices];  // device address of g_kc_static_scratch, per device
+
+// Device address of the static scratch on device `dev` (the current device).
+// Host code cannot use the symbol itself: it names a host-side shadow.
+int static_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kStaticMaxDevices) return KC_E_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_kc_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress");
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return KC_OK;
+}
+
+// Rows must be strictly ascending, above their own rank and below n.
+__global__ void k_check_dag(const uint64_t* __restrict__ orow, const uint32_t* __restrict__ ocol, uint32_t n,
+                            uint64_t m, uint32_t* status) {
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t b = orow[r], e = orow[r + 1];
+    if (e < b || e > m) {
+      atomicOr(status, kStBadGraph);
+      continue;
+    }
+    uint32_t prev = (uint32_t)r;
+    for (uint64_t p = b; p < e; p++) {
+      const uint32_t v = ocol[p];
+      if (v <= prev || v >= n) {
+        atomicOr(status, kStBadGraph);
+        break;
+      }
+      prev = v;
+    }
+  }
+}
+
+template <int W>
+int static_tier(int num_sms, const EnumKArgs& x, cudaStream_t s) {
+  kc_ctx* ctx = nullptr;  // for KC_CUDA: errors carry no context
+  const int wpb = W <= 4 ? 8 : 4;
+  const size_t smem = warp_state_bytes<W>() * wpb;
+  if (smem > 48 * 1024)
+    KC_CUDA(cudaFuncSetAttribute(k_enum<W, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enum<W, 0>, wpb * 32, smem));
+  uint64_t blocks = (uint64_t)num_sms * std::max(per_sm, 1);
+  blocks = std::max<uint64_t>(1, std::min<uint64_t>(blocks, (x.nroots + wpb - 1) / wpb));
+  k_enum<W, 0><<<(unsigned)blocks, wpb * 32, smem, s>>>(x);
+  KC_CUDA(cudaGetLastError());
+  return KC_OK;
+}
+}  // namespace
+}  // namespace kc
+
+extern "C" int kc_count_dag_noalloc(uint32_t n, const uint64_t* d_orow, const uint32_t* d_ocol, uint32_t k,
+                                    uint64_t* count, void* stream) {
+  using namespace kc;
+  kc_ctx* ctx = nullptr;  // for KC_CUDA: errors carry no context
+  if (!d_orow || !count || k == 0) return KC_E_INVALID_ARG;
+  if (k > KC_MAX_K || n == 0xFFFFFFFFu) return KC_E_UNSUPPORTED;
+  int dev = 0;
+  KC_CUDA(cudaGetDevice(&dev));
+  void* base = nullptr;
+  KC_TRY(static_scratch(dev, &base));
+  int num_sms = 0;
+  KC_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* acc = (unsigned long long*)base;
+  uint32_t* cnts = (uint32_t*)((uint8_t*)base + kStaticAccBytes);
+  uint32_t* status = cnts + 16;
+  uint32_t* lists = (uint32_t*)((uint8_t*)base + kStaticAccBytes + kStaticCntBytes);
+  // the array keeps the previous call's contents: clear accumulators, counts and status
+  KC_CUDA(cudaMemsetAsync(base, 0, kStaticAccBytes + kStaticCntBytes, s));
+  uint64_t ends[2] = {0, 0};
+  KC_CUDA(cudaMemcpyAsync(&ends[0], d_orow, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaMemcpyAsync(&ends[1], d_orow + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaStreamSynchronize(s));
+  if (ends[0] != 0 || ends[1] >= (1ull << 40)) return KC_E_INVALID_GRAPH;
+  const uint64_t m = ends[1];
+  if (m > 0 && !d_ocol) return KC_E_INVALID_ARG;
+  if (n > 0) {
+    const unsigned cb = std::max<uint32_t>(1, std::min<uint32_t>((n + 255) / 256, (uint32_t)num_sms * 8));
+    k_check_dag<<<cb, 256, 0, s>>>(d_orow, d_ocol, n, m, status);
+    KC_CUDA(cudaGetLastError());
+  }
+  uint32_t hstatus = 0;
+  KC_CUDA(cudaMemcpyAsync(&hstatus, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaStreamSynchronize(s));
+  if (hstatus & kStBadGraph) return KC_E_INVALID_GRAPH;
+  if (k == 1) {
+    *count = n;
+    return KC_OK;
+  }
+  if (k == 2) {
+    *count = m;
+    return KC_OK;
+  }
+  EnumKArgs x{};
+  x.orow = d_orow;
+  x.ocol = d_ocol;
+  // the count kernel stores vert[root] without using it; the row offsets,
+  // read as 2n+2 words, are a readable stand-in for that n-word array
+  x.vert = (const uint32_t*)d_orow;
+  x.k = k;
+  x.prune = 1;
+  x.acc = acc;
+  x.status = status;
+  for (uint64_t lo = 0; lo < n; lo += kStaticChunk) {
+    const uint32_t hi = (uint32_t)std::min<uint64_t>(n, lo + kStaticChunk);
+    // per pass: tier counts and root-queue counters start at zero
+    KC_CUDA(cudaMemsetAsync(cnts, 0, 16 * sizeof(uint32_t), s));
+    KC_CUDA(cudaMemsetAsync(&acc[kAccQueue0], 0, kTiers * sizeof(unsigned long long), s));
+    const unsigned bb = std::max<uint32_t>(1, std::min<uint32_t>((hi - (uint32_t)lo + 255) / 256, (uint32_t)num_sms * 8));
+    k_bin_roots<<<bb, 256, 0, s>>>(d_orow, (uint32_t)lo, hi, k - 1, lists, kStaticChunk, cnts, acc);
+    KC_CUDA(cudaGetLastError());
+    uint32_t hcnt[16] = {0};
+    KC_CUDA(cudaMemcpyAsync(hcnt, cnts, sizeof(hcnt), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    // out-degrees above 256 need per-warp state outside shared memory: not in this entry point
+    if (hcnt[4] || hcnt[5] || hcnt[kTiers]) return KC_E_UNSUPPORTED;
+    for (int t = 0; t < 4; t++) {
+      if (!hcnt[t]) continue;
+      EnumKArgs y = x;
+      y.roots = lists + (size_t)t * kStaticChunk;
+      y.nroots = hcnt[t];
+      y.qctr = (unsigned int*)&acc[kAccQueue0 + t];
+      if (t == 0) KC_TRY(static_tier<1>(num_sms, y, s));
+      if (t == 1) KC_TRY(static_tier<2>(num_sms, y, s));
+      if (t == 2) KC_TRY(static_tier<4>(num_sms, y, s));
+      if (t == 3) KC_TRY(static_tier<8>(num_sms, y, s));
+    }
+  }
+  unsigned long long total = 0;
+  KC_CUDA(cudaMemcpyAsync(&total, &acc[kAccCount], sizeof(total), cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaStreamSynchronize(s));
+  *count = total;
+  return KC_OK;
+}

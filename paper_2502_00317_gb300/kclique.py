@@ -38,7 +38,7 @@ KC_MAX_OUTDEG = 1024
 EXPORTS = (
     "kc_create", "kc_destroy", "kc_upload", "kc_free_graph", "kc_graph_info_get", "kc_export_dag",
     "kc_count", "kc_list", "kc_list_range", "kc_last_stats", "kc_last_upload_stats", "kc_strerror",
-    "kc_last_error",
+    "kc_last_error", "kc_count_dag_noalloc",
 )
 
 
@@ -132,6 +132,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kc_last_upload_stats": (i32, [P, ctypes.POINTER(kc_upload_stats)]),
         "kc_strerror": (ctypes.c_char_p, [i32]),
         "kc_last_error": (ctypes.c_char_p, [P]),
+        "kc_count_dag_noalloc": (i32, [u32, P, P, u32, pu64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -246,6 +247,15 @@ def kc_last_upload_stats(ctx: int) -> dict:
     s = kc_upload_stats()
     _check(load().kc_last_upload_stats(ctypes.c_void_p(ctx), ctypes.byref(s)), "kc_last_upload_stats")
     return _struct_dict(s)
+
+
+def kc_count_dag_noalloc(n: int, d_orow, d_ocol, k: int, stream=None) -> int:
+    """Count k-cliques of a device-resident rank-space DAG without any allocation
+    inside the library (for callers that must not allocate); see kclique.h."""
+    c = ctypes.c_uint64(0)
+    _check(load().kc_count_dag_noalloc(int(n), _ptr(d_orow), _ptr(d_ocol), int(k), ctypes.byref(c), _stream(stream)),
+           "kc_count_dag_noalloc")
+    return int(c.value)
 
 
 def kc_last_error(ctx: int) -> str:

@@ -213,29 +213,37 @@ def run_ours(a):
     value = ws * units / (ms / 1e3)
     evalue = ws * units / (ems / 1e3)
     launches = sum(u["launches"] + sum(s["total_launches"] for s in st) for u, st in zip(ups, sts))
-    # dominant kernel family: the per-root enumerator (bitmap build + prune + search)
+    # dominant kernel family: the enumerator (k_enum + k_tasks of every width
+    # tier of one kc_count call; the tiers run concurrently on their own
+    # streams, so their wall time is the events around the whole family)
     enum_ms = statistics.mean(sum(s["ms_enum"] for s in st) for st in sts)
     enum_launch = statistics.mean(sum(s["enum_launches"] for s in st) for st in sts)
-    build_words = sts[0]
-    bw = sum(s["build_words"] for s in build_words)
-    peaks = _peaks()
-    hbm = peaks.get("hbm_gbs")
-    # algorithmic bytes of the enumerator per step: every DAG word gathered for
-    # the root bitmaps (4 B each) plus the root out-lists (counted in the same
-    # counter) -- see the design doc, roofline section
-    achieved_gbs = (bw * 4) / (enum_ms / 1e3) / 1e9 if enum_ms > 0 else None
+    word_ops = statistics.mean(sum(s["word_ops"] for s in st) for st in sts)
+    calls = len(ks)
+    peak_ops, peak_note = word_op_peak()
+    achieved = (word_ops / calls) / (enum_ms / calls / 1e3) / 1e9 if enum_ms > 0 else None
     roof = {
-        "kernel": "k_enum (per-root bitmap build + Alg.5 prune + search/memo), all tiers of one step",
-        "bound": "hbm",
-        "achieved": round(achieved_gbs, 2) if achieved_gbs else None,
-        "peak": hbm,
-        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6800 GB/s",
-        "unit": "GB/s",
-        "frac": round(achieved_gbs / (hbm or 6800.0), 4) if achieved_gbs else None,
+        "kernel": "enumerator family (k_enum + k_tasks, all width tiers of one kc_count call)",
+        "bound": "alu",
+        "achieved": round(achieved, 3) if achieved else None,
+        "peak": round(peak_ops / 1e9, 1) if peak_ops else None,
+        "peak_source": peak_note,
+        "unit": "Gword-op/s (word-op = 32-bit AND + POPC of candidate words)",
+        "frac": round(achieved * 1e9 / peak_ops, 5) if (achieved and peak_ops) else None,
         "traffic": None,
-        "enum_ms_per_step": round(enum_ms, 3),
+        "word_ops_per_launch": round(word_ops / calls),
+        "ms_per_launch": round(enum_ms / calls, 3),
         "enum_launches_per_step": enum_launch,
     }
+    # upload stages are HBM-bound: algorithmic bytes of peel + orient per step
+    hbm = _peaks().get("hbm_gbs")
+    m_und = int(g.rowptr[-1]) // 2
+    up_bytes = (8 * (n + 1) + 4 * 2 * m_und) + 4 * 2 * m_und + (8 * (n + 1) + 4 * m_und) + 12 * n
+    up_ms = statistics.mean(u["ms_peel"] + u["ms_orient"] for u in ups)
+    roof_upload = {"kernel": "k_peel + orient (a2-a3)", "bound": "hbm",
+                   "achieved": round(up_bytes / (up_ms / 1e3) / 1e9, 2), "peak": hbm, "unit": "GB/s",
+                   "frac": round(up_bytes / (up_ms / 1e3) / 1e9 / hbm, 4) if hbm else None,
+                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "algorithmic_bytes": up_bytes}
     line = {
         "metric": METRIC,
         "value": value,
@@ -258,6 +266,7 @@ def run_ours(a):
         "gpu_launches": launches,
         "clocks": clocks,
         "roofline": roof,
+        "roofline_upload": roof_upload,
         "stage_ms": {"upload": statistics.mean(u["ms_total"] for u in ups),
                      "peel": statistics.mean(u["ms_peel"] for u in ups),
                      "enum_per_k": [round(statistics.mean(st[i]["ms_enum"] for st in sts), 3) for i in range(len(ks))],
@@ -271,6 +280,26 @@ def run_ours(a):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def word_op_peak():
+    """Measured word-op rate of this GPU (libkc_peak.so: an AND + POPC loop at full occupancy)."""
+    import ctypes
+
+    from paper_2502_00317_gb300 import build as b
+
+    try:
+        lib = ctypes.CDLL(b.build_peak())
+        f = lib.kc_peak_word_ops
+        f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                      ctypes.POINTER(ctypes.c_float)]
+        rate, per, ms = ctypes.c_double(), ctypes.c_double(), ctypes.c_float()
+        st = f(4096, 5, ctypes.byref(rate), ctypes.byref(per), ctypes.byref(ms))
+        if st != 0:
+            return None, f"kc_peak failed ({st})"
+        return rate.value, f"measured: kc_peak_word_ops, best of 5 launches of {ms.value:.2f} ms (burst)"
+    except Exception as e:  # pragma: no cover
+        return None, f"kc_peak unavailable: {e}"
 
 
 def cpu_baseline(g, ks=(5, 6)):

@@ -86,6 +86,7 @@ typedef struct kc_stats {
   uint64_t memo_frames;    /* memoised frames opened (device trie walks) */
   float ms_tier[6];        /* device time of each width tier (1, 2, 4, 8, 16, 32 words) */
   uint32_t roots_tier[6];  /* roots in each width tier */
+  uint64_t word_ops;       /* 32-bit candidate words intersected (AND + POPC) by the enumerator */
 } kc_stats;
 
 /* Per-stage device times of the last kc_upload (CUDA events). */

@@ -18,6 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkc.so")
 SOURCES = ["kc_api.cu", "kc_prep.cu", "kc_enum.cu"]
+PEAK_SOURCE = "kc_peak.cu"  # separate library: the benchmark's integer-pipe peak
+PEAK_LIB = os.path.join(BUILD, "libkc_peak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,13 +36,27 @@ def _flags(extra=()):
 
 def _digest() -> str:
     h = hashlib.sha256()
-    for name in sorted(os.listdir(CSRC)) + [os.path.join("..", "..", "include", "kclique.h")]:
+    for name in sorted(set(os.listdir(CSRC)) - {PEAK_SOURCE}) + [os.path.join("..", "..", "include", "kclique.h")]:
         p = os.path.normpath(os.path.join(CSRC, name))
         if os.path.isfile(p):
             h.update(name.encode())
             h.update(open(p, "rb").read())
     h.update(" ".join(_flags()).encode())
     return h.hexdigest()
+
+
+def build_peak(force: bool = False) -> str:
+    """Compile libkc_peak.so (the integer-pipe peak microbenchmark) and return its path."""
+    os.makedirs(BUILD, exist_ok=True)
+    src = os.path.join(CSRC, PEAK_SOURCE)
+    if force or not os.path.exists(PEAK_LIB) or os.path.getmtime(PEAK_LIB) < os.path.getmtime(src):
+        tmp = PEAK_LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc(), *_flags(), "-shared", src, "-o", tmp, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {PEAK_SOURCE}:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, PEAK_LIB)
+    return PEAK_LIB
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:

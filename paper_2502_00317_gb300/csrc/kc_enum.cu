@@ -138,15 +138,17 @@ __device__ __forceinline__ uint32_t word_at(const uint32_t (&c)[W], uint32_t i) 
   return r;
 }
 
-// Number of edges of G[S] (the 2-cliques of S); lane-partial.
+// Number of edges of G[S] (the 2-cliques of S); lane-partial.  `ops` counts
+// the candidate words intersected (AND + POPC), the enumerator's work unit.
 template <int W>
-__device__ __forceinline__ uint32_t edges_partial(const uint32_t (&S)[W], const uint32_t* rows) {
+__device__ __forceinline__ uint32_t edges_partial(const uint32_t (&S)[W], const uint32_t* rows, uint32_t& ops) {
   const uint32_t lane = lane_id();
   uint32_t c = 0;
 #pragma unroll
   for (int w = 0; w < W; w++) {
     if ((S[w] >> lane) & 1u) {
       const uint32_t* rv = rows + (size_t)((w << 5) + lane) * W;
+      ops += W - w;
 #pragma unroll
       for (int w2 = w; w2 < W; w2++) c += __popc(S[w2] & rv[w2]);
     }
@@ -255,13 +257,15 @@ __device__ __forceinline__ int select_bit(const uint32_t (&c)[W], int j) {
 // vertices v of S that can start a 3-clique (r_v >= 3) and each counts the
 // edges of S ∩ row(v) on its own.
 template <int W>
-__device__ __forceinline__ uint32_t tri_partial(const uint32_t (&S)[W], const uint32_t* rows, const uint32_t* m3) {
+__device__ __forceinline__ uint32_t tri_partial(const uint32_t (&S)[W], const uint32_t* rows, const uint32_t* m3,
+                                               uint32_t& ops) {
   const uint32_t lane = lane_id();
   uint32_t acc = 0;
 #pragma unroll
   for (int w = 0; w < W; w++) {
     if (((S[w] & m3[w]) >> lane) & 1u) {
       const uint32_t* rv = rows + (size_t)((w << 5) + lane) * W;
+      ops += W - w;
       uint32_t T[W];
 #pragma unroll
       for (int q = 0; q < W; q++) T[q] = (q < w) ? 0u : (S[q] & rv[q]);
@@ -272,6 +276,7 @@ __device__ __forceinline__ uint32_t tri_partial(const uint32_t (&S)[W], const ui
           const int b = __ffs(y) - 1;
           y &= y - 1;
           const uint32_t* rw = rows + (size_t)((q << 5) + b) * W;
+          ops += W - q;
 #pragma unroll
           for (int q2 = q; q2 < W; q2++) acc += __popc(T[q2] & rw[q2]);
         }
@@ -283,6 +288,8 @@ __device__ __forceinline__ uint32_t tri_partial(const uint32_t (&S)[W], const ui
 
 struct Acc {
   unsigned long long cnt = 0, sum = 0;
+  uint32_t ops = 0;          // candidate words intersected since the last fold into ops64
+  unsigned long long ops64 = 0;
   unsigned long long pruned = 0, words = 0, hits = 0, ins = 0, full = 0, frames = 0, heavy = 0, tasks = 0;
 };
 
@@ -377,15 +384,16 @@ __device__ __forceinline__ void all_bits(int d, uint32_t (&S)[W]) {
 
 // Count of the cl-cliques of G[c] for cl <= 3, summed over the warp.
 template <int W>
-__device__ __forceinline__ unsigned long long small_count(const WarpState<W>& st, const uint32_t (&c)[W], uint32_t cl) {
+__device__ __forceinline__ unsigned long long small_count(const WarpState<W>& st, const uint32_t (&c)[W], uint32_t cl,
+                                                          Acc& acc) {
   if (cl == 1) {
     uint32_t s = 0;
 #pragma unroll
     for (int w = 0; w < W; w++) s += __popc(c[w]);
     return s;
   }
-  if (cl == 2) return warp_sum(edges_partial<W>(c, st.rows));
-  return warp_sum(tri_partial<W>(c, st.rows, st.masks + 3 * W));
+  if (cl == 2) return warp_sum(edges_partial<W>(c, st.rows, acc.ops));
+  return warp_sum(tri_partial<W>(c, st.rows, st.masks + 3 * W, acc.ops));
 }
 
 // Open a memoised frame for (c, cl): a stored whole key is a retrieval (returns
@@ -439,8 +447,9 @@ __device__ bool memo_open(const Memo& memo, const uint32_t (&c)[W], uint32_t cl,
 
 // Eq. (1) for a candidate set c needing cl-cliques: 2 cl |E| > (cl - 1) |V|^2.
 template <int W>
-__device__ __forceinline__ bool eq1_dense(const WarpState<W>& st, const uint32_t (&c)[W], uint32_t cl, uint32_t sz) {
-  uint32_t e = warp_sum(edges_partial<W>(c, st.rows));
+__device__ __forceinline__ bool eq1_dense(const WarpState<W>& st, const uint32_t (&c)[W], uint32_t cl, uint32_t sz,
+                                          Acc& acc) {
+  uint32_t e = warp_sum(edges_partial<W>(c, st.rows, acc.ops));
   return 2ull * cl * e > (unsigned long long)(cl - 1) * sz * sz;
 }
 
@@ -459,8 +468,8 @@ __device__ void dfs_plain(WarpState<W>& st, const EnumKArgs& a, int base, Acc& a
       uint32_t s[W];
 #pragma unroll
       for (int w = 0; w < W; w++) s[w] = S[w];
-      if (l == 3) acc.cnt += tri_partial<W>(s, st.rows, st.masks + 3 * W);
-      else if (l == 2) acc.cnt += edges_partial<W>(s, st.rows);
+      if (l == 3) acc.cnt += tri_partial<W>(s, st.rows, st.masks + 3 * W, acc.ops);
+      else if (l == 2) acc.cnt += edges_partial<W>(s, st.rows, acc.ops);
       else if (lane == 0) {
         uint32_t c = 0;
 #pragma unroll
@@ -544,6 +553,7 @@ __device__ void dfs_plain(WarpState<W>& st, const EnumKArgs& a, int base, Acc& a
       sz += __popc(c[w]);
       anym |= c[w] & mk[w];
     }
+    if (lane == 0) acc.ops += W;
     __syncwarp();
     if (lane == 0) st.pos[depth] = v - 1;
     if (sz >= l - 1 && anym) {
@@ -628,6 +638,7 @@ __device__ unsigned long long dfs_memo(WarpState<W>& st, const EnumKArgs& a, con
       c[w] = S[w] & rv[w];
       sz += __popc(c[w]);
     }
+    if (lane == 0) acc.ops += W;
     const uint32_t cl = l - 1;
     unsigned long long val = 0;
     bool resolved = true;
@@ -635,14 +646,14 @@ __device__ unsigned long long dfs_memo(WarpState<W>& st, const EnumKArgs& a, con
     unsigned long long start_sum = 0;
     int start_pos = -1;
     if (cl <= 3) {
-      val = sz >= cl ? small_count<W>(st, c, cl) : 0ull;
+      val = sz >= cl ? small_count<W>(st, c, cl, acc) : 0ull;
     } else {
       uint32_t anym = 0;
       const uint32_t* mk = st.masks + cl * W;
 #pragma unroll
       for (int w = 0; w < W; w++) anym |= c[w] & mk[w];
       if (sz >= cl && anym) {
-        cd = fd || (a.memo && eq1_dense<W>(st, c, cl, sz));
+        cd = fd || (a.memo && eq1_dense<W>(st, c, cl, sz, acc));
         if (cd) {
           if (memo_open<W>(memo, c, cl, &start_sum, &start_pos, acc)) val = start_sum;
           else resolved = false;
@@ -701,10 +712,11 @@ __device__ void run_branch(WarpState<W>& st, const EnumKArgs& a, const Memo& mem
     c[w] = S0[w] & rv[w];
     sz += __popc(c[w]);
   }
+  if (lane == 0) acc.ops += W;
   const uint32_t cl = need - 1;
   if (sz < cl) return;
   if (MODE != 1 && cl <= 3) {
-    unsigned long long v = small_count<W>(st, c, cl);
+    unsigned long long v = small_count<W>(st, c, cl, acc);
     if (lane == 0) acc.cnt += v;
     return;
   }
@@ -727,7 +739,7 @@ __device__ void run_branch(WarpState<W>& st, const EnumKArgs& a, const Memo& mem
     return;
   }
   // MODE 2
-  bool cd = a.memo && eq1_dense<W>(st, c, cl, sz);
+  bool cd = a.memo && eq1_dense<W>(st, c, cl, sz, acc);
   unsigned long long ssum = 0;
   int spos = top_bit<W>(c);
   if (cd && memo_open<W>(memo, c, cl, &ssum, &spos, acc)) {
@@ -816,7 +828,9 @@ __device__ void flush_acc(const EnumKArgs& a, Acc& acc) {
   unsigned long long cnt = warp_sum(acc.cnt);
   unsigned long long sum = warp_sum(acc.sum);
   unsigned long long words = warp_sum(acc.words);
+  unsigned long long ops = warp_sum(acc.ops64 + acc.ops);
   if (lane == 0) {
+    if (ops) atomicAdd(&a.acc[kAccWordOps], ops);
     if (cnt) atomicAdd(&a.acc[kAccCount], cnt);
     if (sum) atomicAdd(&a.acc[kAccChecksum], sum);
     if (acc.pruned) atomicAdd(&a.acc[kAccRootsPruned], acc.pruned);
@@ -912,7 +926,7 @@ __global__ void __launch_bounds__(256) k_enum(EnumKArgs a) {
       dfs_plain<W, MODE>(st, a, 0, acc);
     } else {
       if (need <= 3) {
-        unsigned long long v = small_count<W>(st, S0, need);
+        unsigned long long v = small_count<W>(st, S0, need, acc);
         if (lane == 0) acc.cnt += v;
       } else {
         if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
@@ -927,6 +941,8 @@ __global__ void __launch_bounds__(256) k_enum(EnumKArgs a) {
         if (lane == 0) acc.cnt += v;
       }
     }
+    acc.ops64 += acc.ops;
+    acc.ops = 0;
     __syncwarp();
   }
   flush_acc<W>(a, acc);
@@ -984,6 +1000,8 @@ __global__ void __launch_bounds__(256) k_tasks(EnumKArgs a) {
       if (MODE == 2) next_epoch(memo, &epoch);
     }
     run_branch<W, MODE>(st, a, memo, u, d, v1, acc);
+    acc.ops64 += acc.ops;
+    acc.ops = 0;
     __syncwarp();
   }
   flush_acc<W>(a, acc);
@@ -1266,6 +1284,7 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
   stt.memo_full = ctx->h_acc[kAccMemoFull];
   stt.memo_frames = ctx->h_acc[kAccMemoFrames];
   stt.roots_heavy = ctx->h_acc[kAccRootsHeavy];
+  stt.word_ops = ctx->h_acc[kAccWordOps];
   if (k >= 2) {
     for (int t = 0; t < kTiers; t++) {
       stt.roots_tier[t] = tier_roots[t];

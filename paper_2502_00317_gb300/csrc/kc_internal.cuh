@@ -155,6 +155,7 @@ enum AccSlot : int {
   kAccMemoFull,
   kAccMemoFrames,
   kAccTasks,
+  kAccWordOps,
   kAccQueue0,      // root-queue counters (one per width tier)
   kAccArena0 = kAccQueue0 + kTiers,     // split path: arena units used, per tier
   kAccTaskUsed0 = kAccArena0 + kTiers,  // split path: tasks queued, per tier

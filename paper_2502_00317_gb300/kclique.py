@@ -87,6 +87,7 @@ class kc_stats(ctypes.Structure):
         ("memo_frames", ctypes.c_uint64),
         ("ms_tier", ctypes.c_float * 6),
         ("roots_tier", ctypes.c_uint32 * 6),
+        ("word_ops", ctypes.c_uint64),
     ]
 
 

@@ -68,8 +68,8 @@ def test_create_fails_cleanly_without_gpu():
 
 
 def test_struct_sizes_match_header():
-    # kc_opts: 4 x u32 + 2 x u64 = 32 bytes; kc_stats: 3 f32 + 2 u32 + 8 u64 + 6 f32 + 6 u32 = 136 bytes
+    # kc_opts: 4 x u32 + 2 x u64 = 32 bytes; kc_stats: 3 f32 + 2 u32 + 8 u64 + 6 f32 + 6 u32 + 1 u64 = 144 bytes
     assert ctypes.sizeof(kc.kc_opts) == 32
     assert ctypes.sizeof(kc.kc_graph_info) == 24
-    assert ctypes.sizeof(kc.kc_stats) == 136
+    assert ctypes.sizeof(kc.kc_stats) == 144
     assert ctypes.sizeof(kc.kc_upload_stats) == 24

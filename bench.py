@@ -267,6 +267,7 @@ def run_ours(a):
         "clocks": clocks,
         "roofline": roof,
         "roofline_upload": roof_upload,
+        "step_ms": [round(t, 3) for t in times],
         "stage_ms": {"upload": statistics.mean(u["ms_total"] for u in ups),
                      "peel": statistics.mean(u["ms_peel"] for u in ups),
                      "enum_per_k": [round(statistics.mean(st[i]["ms_enum"] for st in sts), 3) for i in range(len(ks))],

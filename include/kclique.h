@@ -65,7 +65,7 @@ typedef struct kc_graph_info {
   uint32_t degeneracy;     /* delta(G): the largest core number (Sec. II-A) */
   uint64_t m;              /* undirected edges after canonicalisation */
   uint32_t max_out_degree; /* of the degeneracy DAG; <= degeneracy */
-  uint32_t peel_rounds;    /* parallel peeling rounds used */
+  uint32_t peel_rounds;    /* grid-wide peeling sub-rounds (barriers) used */
 } kc_graph_info;
 
 /* Telemetry of the last kc_count / kc_list call on a context (device times
@@ -116,8 +116,9 @@ int kc_destroy(kc_ctx* ctx);
  * entries with ids < n are accepted and cleaned on the device.
  *
  * The upload then computes on the device, with no host round trip per round:
- *   - the degeneracy order (Sec. II-A) by parallel k-core peeling, order key
- *     (core number, peeling round, id);
+ *   - the degeneracy order (Sec. II-A) by parallel k-core peeling, level by
+ *     level: order key (core number, position of removal within its level;
+ *     the second part depends on timing, no count does);
  *   - the DAG based on it (Sec. II-A), relabelled to rank space, each out-list
  *     sorted ascending (Algorithm 2, first line).
  * *out receives the handle.  Synchronises the stream.

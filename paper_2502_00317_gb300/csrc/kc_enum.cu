@@ -81,13 +81,15 @@ struct WarpState {
   uint8_t* rr;                // [32W] r values (Algorithm 5), capped at k
   uint8_t* dense;             // [KMAX] frame uses the memo
   uint8_t* fullins;           // [KMAX] frame's whole set already stored
+  uint32_t* crow;             // [32] rows of a candidate set re-indexed to 0..31 (count_compact)
   __host__ __device__ static constexpr size_t bytes() {
     return (size_t)32 * W * 4 + (size_t)32 * W * W * 4 + (size_t)KMAX * W * 4 * 2 + (size_t)KMAX * 8 +
-           (size_t)KMAX * 4 * 2 + (size_t)(KMAX + 1) * 4 + KMAX + 32 * W + KMAX * 2 + 16;
+           (size_t)KMAX * 4 * 2 + (size_t)(KMAX + 1) * 4 + KMAX + 32 * W + KMAX * 2 + 16 + 32 * 4;
   }
   __device__ void carve(uint8_t* base) {
     uint8_t* p = base;
     sum = (unsigned long long*)p; p += (size_t)KMAX * 8;
+    crow = (uint32_t*)p; p += 32 * 4;
     nbr = (uint32_t*)p; p += (size_t)32 * W * 4;
     rows = (uint32_t*)p; p += (size_t)32 * W * W * 4;
     masks = (uint32_t*)p; p += (size_t)KMAX * W * 4;
@@ -286,6 +288,45 @@ __device__ __forceinline__ uint32_t tri_partial(const uint32_t (&S)[W], const ui
   return acc;
 }
 
+// Cliques of size need + 1 whose smallest vertex is the caller's, given its
+// candidate word c0 in a graph of at most 32 vertices with one 32-bit row of
+// larger neighbours per vertex (R): a depth-first search of this lane alone,
+// each step one AND + POPC on a single word; the last two picks are counted
+// as the edges of the candidate set.  need >= 1.
+__device__ __forceinline__ uint32_t lane_count(const uint32_t* R, uint32_t c0, uint32_t need, uint32_t& ops) {
+  if (need == 1) return __popc(c0);
+  uint32_t stk[KMAX];
+  uint32_t cnt = 0;
+  int d = 0;
+  stk[0] = c0;
+  while (d >= 0) {
+    uint32_t c = stk[d];
+    const uint32_t rem = need - (uint32_t)d;  // vertices still to pick from c
+    if (rem == 2) {
+      uint32_t x = c;
+      while (x) {
+        const int j = __ffs(x) - 1;
+        x &= x - 1;
+        cnt += __popc(x & R[j]);
+        ops++;
+      }
+      d--;
+      continue;
+    }
+    if ((uint32_t)__popc(c) < rem) {
+      d--;
+      continue;
+    }
+    const int j = __ffs(c) - 1;
+    c &= c - 1;
+    stk[d] = c;
+    const uint32_t nc = c & R[j];
+    ops++;
+    if ((uint32_t)__popc(nc) >= rem - 1) stk[++d] = nc;
+  }
+  return cnt;
+}
+
 struct Acc {
   unsigned long long cnt = 0, sum = 0;
   uint32_t ops = 0;          // candidate words intersected since the last fold into ops64
@@ -305,23 +346,48 @@ __device__ bool build_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, int
   __syncwarp();
   const uint32_t last = st.nbr[d - 1];
   uint32_t words = 0;
-  for (int i = 0; i < d - 1; i++) {
-    const uint32_t v = st.nbr[i];
-    const uint64_t b = a.orow[v], e = a.orow[v + 1];
-    for (uint64_t p0 = b; p0 < e; p0 += 32) {
-      uint64_t p = p0 + lane;
-      uint32_t w = p < e ? a.ocol[p] : 0xFFFFFFFFu;
-      words += (p < e);
-      if (w <= last) {
-        int lo = i + 1, hi = d;  // search nbr[i+1 .. d)
-        while (lo < hi) {
-          int mid = (lo + hi) >> 1;
-          if (st.nbr[mid] < w) lo = mid + 1;
-          else hi = mid;
+  if (W == 1) {
+    // at most 31 rows: the warp reads each out-list 32 entries at a time and
+    // places each entry by a binary search in nbr (ranks above the row)
+    for (int i = 0; i < d - 1; i++) {
+      const uint32_t v = st.nbr[i];
+      const uint64_t b = a.orow[v], e = a.orow[v + 1];
+      for (uint64_t p0 = b; p0 < e; p0 += 32) {
+        const uint64_t p = p0 + lane;
+        const uint32_t w = p < e ? __ldg(&a.ocol[p]) : 0xFFFFFFFFu;
+        words += (p < e);
+        if (w <= last) {
+          int lo = i + 1, hi = d;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (st.nbr[mid] < w) lo = mid + 1;
+            else hi = mid;
+          }
+          if (lo < d && st.nbr[lo] == w) atomicOr(&st.rows[(size_t)i * W + (lo >> 5)], 1u << (lo & 31));
         }
-        if (lo < d && st.nbr[lo] == w) atomicOr(&st.rows[(size_t)i * W + (lo >> 5)], 1u << (lo & 31));
+        if (__all_sync(0xFFFFFFFFu, w > last)) break;
       }
-      if (__all_sync(0xFFFFFFFFu, w > last)) break;
+    }
+  } else {
+    // one lane per row: row i holds the positions j > i with nbr[j] in
+    // N+(nbr[i]), found by merging the two ascending lists; 32 rows at once
+    for (int i = lane; i < d - 1; i += 32) {
+      const uint32_t v = st.nbr[i];
+      const uint64_t b = a.orow[v], e = a.orow[v + 1];
+      uint32_t* row = st.rows + (size_t)i * W;
+      int j = i + 1;
+      uint64_t p = b;
+      while (p < e && j < d) {
+        const uint32_t w = __ldg(&a.ocol[p]);
+        if (w > last) break;
+        while (j < d && st.nbr[j] < w) j++;
+        if (j < d && st.nbr[j] == w) {
+          row[j >> 5] |= 1u << (j & 31);
+          j++;
+        }
+        p++;
+      }
+      words += (uint32_t)(p - b);
     }
   }
   acc.words += words;
@@ -371,6 +437,45 @@ __device__ bool build_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, int
   }
   __syncwarp();
   return true;
+}
+
+// Number of l-cliques (l >= 2) of G[S] for |S| = m <= 32, lane-partial (the
+// lanes' values add up to it).  S is re-indexed to 0..m-1 in ascending order
+// with one 32-bit row each, built by one ballot per vertex (lane j answers
+// whether the vertex's row holds vertex j); lane i then counts the cliques
+// whose smallest vertex is its vertex i on its own (lane_count).  At width 1
+// the root-local indices already fit one word and only the mask by S is
+// needed.  Called by the whole warp.
+// Largest clique size counted by count_compact.  Its lane-local search has no
+// memo, so its work grows like C(m, l - 1) on a dense set; up to 4 that stays
+// below C(31, 3) steps per lane, and larger sizes go through the warp-level
+// search (and the memo, where Eq. (1) calls for it) until they shrink to 4.
+constexpr uint32_t kCompactMaxL = 4;
+
+template <int W>
+__device__ uint32_t count_compact(const WarpState<W>& st, const uint32_t (&S)[W], uint32_t m, uint32_t l,
+                                  uint32_t& ops) {
+  const uint32_t lane = lane_id();
+  uint32_t myrow = 0;
+  bool start;
+  if (W == 1) {
+    start = (S[0] >> lane) & 1u;
+    if (start) myrow = st.rows[lane] & S[0];
+  } else {
+    start = lane < m;
+    const int sv = start ? select_bit<W>(S, (int)lane) : 0;
+    for (uint32_t i = 0; i + 1 < m; i++) {
+      const int si = __shfl_sync(0xFFFFFFFFu, sv, (int)i);
+      const bool bit = start && lane > i && ((st.rows[(size_t)si * W + (sv >> 5)] >> (sv & 31)) & 1u);
+      const uint32_t b = __ballot_sync(0xFFFFFFFFu, bit);
+      if (lane == i) myrow = b;
+    }
+  }
+  st.crow[lane] = myrow;
+  __syncwarp();
+  const uint32_t c = start ? lane_count(st.crow, myrow, l - 1, ops) : 0u;
+  __syncwarp();  // crow is rewritten by the next call
+  return c;
 }
 
 template <int W>
@@ -464,6 +569,19 @@ __device__ void dfs_plain(WarpState<W>& st, const EnumKArgs& a, int base, Acc& a
   while (depth >= base) {
     const uint32_t l = need - depth;  // vertices still to pick from cand[depth]
     const uint32_t* S = st.cand + depth * W;
+    if (MODE == 0 && l >= 3 && l <= kCompactMaxL) {
+      uint32_t s[W], m = 0;
+#pragma unroll
+      for (int w = 0; w < W; w++) {
+        s[w] = S[w];
+        m += __popc(s[w]);
+      }
+      if (m <= 32) {
+        acc.cnt += count_compact<W>(st, s, m, l, acc.ops);
+        depth--;
+        continue;
+      }
+    }
     if (MODE == 0 && l <= 3) {
       uint32_t s[W];
 #pragma unroll
@@ -646,7 +764,9 @@ __device__ unsigned long long dfs_memo(WarpState<W>& st, const EnumKArgs& a, con
     unsigned long long start_sum = 0;
     int start_pos = -1;
     if (cl <= 3) {
-      val = sz >= cl ? small_count<W>(st, c, cl, acc) : 0ull;
+      if (sz < cl) val = 0;
+      else if (cl == 3 && sz <= 32) val = warp_sum(count_compact<W>(st, c, sz, cl, acc.ops));
+      else val = small_count<W>(st, c, cl, acc);
     } else {
       uint32_t anym = 0;
       const uint32_t* mk = st.masks + cl * W;
@@ -654,7 +774,9 @@ __device__ unsigned long long dfs_memo(WarpState<W>& st, const EnumKArgs& a, con
       for (int w = 0; w < W; w++) anym |= c[w] & mk[w];
       if (sz >= cl && anym) {
         cd = fd || (a.memo && eq1_dense<W>(st, c, cl, sz, acc));
-        if (cd) {
+        if (!cd && sz <= 32 && cl <= kCompactMaxL) {
+          val = warp_sum(count_compact<W>(st, c, sz, cl, acc.ops));
+        } else if (cd) {
           if (memo_open<W>(memo, c, cl, &start_sum, &start_pos, acc)) val = start_sum;
           else resolved = false;
         } else {
@@ -715,6 +837,11 @@ __device__ void run_branch(WarpState<W>& st, const EnumKArgs& a, const Memo& mem
   if (lane == 0) acc.ops += W;
   const uint32_t cl = need - 1;
   if (sz < cl) return;
+  if (MODE != 1 && cl >= 3 && cl <= kCompactMaxL && sz <= 32 &&
+      (MODE == 0 || !(a.memo && cl > 3 && eq1_dense<W>(st, c, cl, sz, acc)))) {
+    acc.cnt += count_compact<W>(st, c, sz, cl, acc.ops);
+    return;
+  }
   if (MODE != 1 && cl <= 3) {
     unsigned long long v = small_count<W>(st, c, cl, acc);
     if (lane == 0) acc.cnt += v;
@@ -905,7 +1032,8 @@ __global__ void __launch_bounds__(256) k_enum(EnumKArgs a) {
       dense0 = 2ull * need * er > (unsigned long long)(need - 1) * d * d;
     }
     // heavy roots go to the split path: one task per first-level branch
-    if (a.split_wedges && d > a.split_min_d && !dense0 && need >= 4) {
+    // dense roots keep their memo whole unless they are wide (more than 64 out-neighbours)
+    if (a.split_wedges && d > a.split_min_d && (!dense0 || W >= 4) && need >= 4) {
       uint32_t wg = 0;
       for (int i = lane; i < d; i += 32) {
         uint32_t p = 0;
@@ -914,9 +1042,14 @@ __global__ void __launch_bounds__(256) k_enum(EnumKArgs a) {
         wg += p * (p - 1) / 2;
       }
       wg = warp_sum(wg);
-      if (wg > a.split_wedges && publish_root<W, MODE>(st, a, u, d, acc)) continue;
+      // a wide dense root's search grows with k: its threshold halves for every k above 5
+      const uint32_t thr = dense0 ? (a.split_wedges >> min(need - 4u, 12u)) : a.split_wedges;
+      if (wg > thr && publish_root<W, MODE>(st, a, u, d, acc)) continue;
     }
-    if (MODE == 0 || MODE == 1) {
+    if (MODE != 1 && need >= 2 && need <= kCompactMaxL && d <= 32 && !dense0) {
+      // the whole root at once: one word per row, lanes take the smallest vertex
+      acc.cnt += count_compact<W>(st, S0, (uint32_t)d, need, acc.ops);
+    } else if (MODE == 0 || MODE == 1) {
       if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
       if (lane == 0) {
         st.pos[0] = d - 1;

@@ -468,13 +468,25 @@ __global__ void k_canon_compact(const uint64_t* __restrict__ ptr, const uint32_t
 }
 
 // =================================================================== peel
-// Level-synchronous k-core peeling in one cooperative launch.  Round r at
-// level k: (A) every block counts, over its slice of the id-ordered alive
-// list, the vertices of current degree <= k and the minimum degree of the
-// rest; (B) the frontier (degree <= k) is compacted in id order, its
-// vertices get core k and consecutive ranks; (C) the frontier's alive
-// neighbours lose one degree each.  An empty frontier raises k to the
-// smallest remaining degree.  The order key is (core, round, id).
+// k-core peeling in one cooperative launch, one level k at a time (Sec. II-A:
+// repeatedly remove a vertex of minimum degree; removing every vertex of
+// degree <= k before any of degree > k gives the same core numbers).
+//
+// Level k: every block scans its slice of the vertices and claims (CAS on
+// core[]) the live ones of degree <= k into a shared-memory wave buffer.  A
+// block then removes its wave -- consecutive ranks from one atomic per wave,
+// and one degree decrement for every live neighbour of degree > k.  A
+// neighbour whose degree falls from k+1 to k is claimed and joins the block's
+// next wave at once, so cascades inside a level need no grid-wide barrier.
+// Waves that outgrow the buffer spill to a global list, which every block
+// shares out after a barrier.  A level ends when no block has work and the
+// spill list is empty (one barrier per level when nothing spills).
+//
+// A vertex removed at level k keeps at most k live neighbours, so every
+// out-degree of the resulting DAG is at most the degeneracy.  The order key
+// is (core number, position of removal within the level); the second part
+// depends on timing, which changes no count (any total order gives the same
+// cliques, Sec. II-A).
 struct PeelArgs {
   const uint64_t* rowptr;
   const uint32_t* col;
@@ -483,128 +495,159 @@ struct PeelArgs {
   uint32_t* core;
   uint32_t* rank;
   uint32_t* vert;
-  uint32_t* alive0;
-  uint32_t* alive1;
-  uint32_t* frontier;
-  uint32_t* blkcnt;   // [2][2*nblocks]
-  uint32_t* minrem;   // [3]
+  uint32_t* spill0;   // [n] spill lists of even / odd sub-rounds
+  uint32_t* spill1;
+  uint32_t* ctr;      // [0..2] spill counts, [4..6] removals, per sub-round (rotating); [3] ranks given
   uint32_t* bar;      // [2] count, generation
   uint32_t* status;
-  uint32_t* result;   // [0] degeneracy, [1] rounds
+  uint32_t* result;   // [0] degeneracy, [1] grid-wide sub-rounds
   unsigned long long spin_limit;  // ns
 };
 
 constexpr int kPeelThreads = 512;
+constexpr uint32_t kPeelWave = 2048;  // shared-memory wave buffer entries
+constexpr uint32_t kPeelBig = 512;    // vertices of higher degree are removed by the whole block
+constexpr uint32_t kPeelBigMax = 64;  // big vertices per wave handled block-wide (the rest: one warp each)
+
+__device__ __forceinline__ void peel_push(uint32_t* buf, uint32_t* cnt, uint32_t v, uint32_t* spill,
+                                          uint32_t* spill_cnt) {
+  const uint32_t p = atomicAdd(cnt, 1u);
+  if (p < kPeelWave) {
+    buf[p] = v;
+  } else {
+    spill[atomicAdd(spill_cnt, 1u)] = v;
+  }
+}
+
+// Removal of v's edges [b, e) by the threads t = first, first + stride, ...:
+// every live neighbour of degree > k loses one; one falling to k is claimed
+// and queued.  Four neighbours per trip, loads issued before the atomics.
+__device__ __forceinline__ void peel_edges(const PeelArgs& a, uint64_t b, uint64_t e, uint32_t first, uint32_t stride,
+                                           uint32_t k, uint32_t* q, uint32_t* qn, uint32_t* spill,
+                                           uint32_t* spill_cnt) {
+  for (uint64_t i0 = b + first; i0 < e; i0 += 4ull * stride) {
+    uint32_t u[4], dg[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const uint64_t p = i0 + (uint64_t)j * stride;
+      u[j] = p < e ? __ldg(&a.col[p]) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) dg[j] = u[j] != 0xFFFFFFFFu ? __ldcg(&a.deg[u[j]]) : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      if (dg[j] <= k) continue;  // past the row end, removed, or already claimed at this level
+      const uint32_t old = atomicSub(&a.deg[u[j]], 1u);
+      if (old == k + 1) {
+        if (atomicCAS(&a.core[u[j]], kAlive, k) == kAlive) peel_push(q, qn, u[j], spill, spill_cnt);
+      } else if (old <= k) {
+        atomicAdd(&a.deg[u[j]], 1u);  // lost a race with another decrement: undo
+      }
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelArgs a) {
-  __shared__ uint32_t s_warp[32];
-  const uint32_t nb = gridDim.x, bid = blockIdx.x;
-  uint32_t* alive = a.alive0;
-  uint32_t* alive_next = a.alive1;
-  uint32_t na = a.n, k = 0, next_rank = 0, round = 0;
-  // every vertex starts alive in id order
-  for (uint32_t i = bid * blockDim.x + threadIdx.x; i < a.n; i += nb * blockDim.x) alive[i] = i;
-  if (bid == 0 && threadIdx.x < 3) a.minrem[threadIdx.x] = 0xFFFFFFFFu;
-  if (!grid_barrier(&a.bar[0], &a.bar[1], nb, a.spin_limit, a.status)) return;
-  while (na > 0) {
-    // ---- A: per-block counts over this block's slice
-    uint32_t per = (na + nb - 1) / nb;
-    uint32_t s0 = min(na, bid * per), s1 = min(na, s0 + per);
-    uint32_t f = 0, mn = 0xFFFFFFFFu;
-    for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
-      uint32_t d = __ldcg(&a.deg[__ldcg(&alive[i])]);
-      if (d <= k) f++;
-      else mn = min(mn, d);
-    }
-    uint32_t ftot;
-    block_exclusive_scan<uint32_t>(f, s_warp, &ftot);
-    mn = warp_min_u32(mn);
-    if ((threadIdx.x & 31) == 0 && mn != 0xFFFFFFFFu) atomicMin(&a.minrem[round % 3], mn);
-    uint32_t* cnt = a.blkcnt + (round & 1) * 2 * nb;
-    if (threadIdx.x == 0) {
-      cnt[bid] = ftot;
-      cnt[nb + bid] = (s1 - s0) - ftot;
-      if (bid == 0) a.minrem[(round + 1) % 3] = 0xFFFFFFFFu;
-    }
-    if (!grid_barrier(&a.bar[0], &a.bar[1], nb, a.spin_limit, a.status)) return;
-    // ---- B: offsets, ordered compaction, core and rank of the frontier
-    uint32_t F = 0, fo = 0, ro = 0;
-    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
-      uint32_t fb = ((volatile uint32_t*)cnt)[b];
-      uint32_t rb = ((volatile uint32_t*)cnt)[nb + b];
-      F += fb;
-      if (b < bid) {
-        fo += fb;
-        ro += rb;
+  __shared__ uint32_t s_q[2][kPeelWave];
+  __shared__ uint32_t s_qn[2];
+  __shared__ uint32_t s_base;
+  __shared__ uint32_t s_big[kPeelBigMax];
+  __shared__ uint32_t s_nbig;
+  const uint32_t nb = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
+  const uint32_t lane = tid & 31u, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  volatile uint32_t* vctr = a.ctr;
+  // Every decision below is taken on values that no block can change until
+  // all blocks have read them (per-sub-round slots, rotated over three), so
+  // all blocks take the same branches and meet at the same barriers.
+  uint32_t k = 0, sub = 0, degen = 0, removed = 0;
+  int cur = 0;
+  while (true) {
+    if (removed >= a.n) break;
+    const uint32_t removed0 = removed;
+    bool first = true;
+    while (true) {
+      // ---- sub-round `sub`: spills go to list sub % 2, counted in ctr[sub % 3];
+      // removals are counted in ctr[4 + sub % 3]
+      uint32_t* spill = (sub & 1u) ? a.spill1 : a.spill0;
+      uint32_t* spill_cnt = &a.ctr[sub % 3];
+      if (bid == 0 && tid == 0) {
+        // the slots of sub-round sub + 1 were last read right after barrier sub - 2
+        a.ctr[(sub + 1) % 3] = 0;
+        a.ctr[4 + (sub + 1) % 3] = 0;
       }
-    }
-    {
-      uint32_t t;
-      block_exclusive_scan<uint32_t>(F, s_warp, &t);
-      F = t;
-      block_exclusive_scan<uint32_t>(fo, s_warp, &t);
-      fo = t;
-      block_exclusive_scan<uint32_t>(ro, s_warp, &t);
-      ro = t;
-    }
-    if (F == 0) {
-      uint32_t m = ((volatile uint32_t*)a.minrem)[round % 3];
-      k = max(k + 1, m);
-      round++;
-      continue;
-    }
-    for (uint32_t t0 = s0; t0 < s1; t0 += blockDim.x) {
-      uint32_t i = t0 + threadIdx.x;
-      uint32_t v = 0;
-      bool in = false, valid = i < s1;
-      if (valid) {
-        v = __ldcg(&alive[i]);
-        in = __ldcg(&a.deg[v]) <= k;
-      }
-      uint32_t tf, tr;
-      uint32_t of = block_exclusive_scan<uint32_t>(in ? 1u : 0u, s_warp, &tf);
-      uint32_t orr = block_exclusive_scan<uint32_t>((valid && !in) ? 1u : 0u, s_warp, &tr);
-      if (valid) {
-        if (in) {
-          uint32_t rk = next_rank + fo + of;
-          a.frontier[fo + of] = v;
-          a.core[v] = k;
-          a.rank[v] = rk;
-          a.vert[rk] = v;
-        } else {
-          alive_next[ro + orr] = v;
+      __syncthreads();
+      if (tid == 0) s_qn[cur] = 0;
+      __syncthreads();
+      if (first) {
+        for (uint64_t v = (uint64_t)bid * blockDim.x + tid; v < a.n; v += (uint64_t)nb * blockDim.x) {
+          if (__ldcg(&a.core[v]) == kAlive && __ldcg(&a.deg[v]) <= k && atomicCAS(&a.core[v], kAlive, k) == kAlive)
+            peel_push(s_q[cur], &s_qn[cur], (uint32_t)v, spill, spill_cnt);
         }
+      } else {
+        // the previous sub-round's spill list, shared out by block
+        const uint32_t prev = sub - 1;
+        const uint32_t cnt = vctr[prev % 3];
+        const uint32_t* list = (prev & 1u) ? a.spill1 : a.spill0;
+        const uint32_t per = (cnt + nb - 1) / nb;
+        const uint32_t lo = min(cnt, bid * per), hi = min(cnt, lo + per);
+        for (uint32_t i = lo + tid; i < hi; i += blockDim.x) peel_push(s_q[cur], &s_qn[cur], __ldcg(&list[i]), spill, spill_cnt);
       }
-      fo += tf;
-      ro += tr;
-    }
-    if (!grid_barrier(&a.bar[0], &a.bar[1], nb, a.spin_limit, a.status)) return;
-    // ---- C: alive neighbours of the frontier lose a degree (warp per vertex)
-    {
-      const uint32_t lane = lane_id();
-      const uint32_t gw = (bid * blockDim.x + threadIdx.x) >> 5;
-      const uint32_t nw = (nb * blockDim.x) >> 5;
-      for (uint32_t i = gw; i < F; i += nw) {
-        uint32_t v = __ldcg(&a.frontier[i]);
-        uint64_t b = a.rowptr[v], e = a.rowptr[v + 1];
-        for (uint64_t idx = b + lane; idx < e; idx += 32) {
-          uint32_t w = a.col[idx];
-          if (__ldcg(&a.core[w]) == kAlive) atomicSub(&a.deg[w], 1u);
+      // ---- waves inside this block
+      while (true) {
+        __syncthreads();
+        const uint32_t cnt = min(s_qn[cur], kPeelWave);
+        if (cnt == 0) break;
+        __syncthreads();
+        if (tid == 0) {
+          s_base = atomicAdd(&a.ctr[3], cnt);
+          atomicAdd(&a.ctr[4 + sub % 3], cnt);
+          s_qn[cur ^ 1] = 0;
+          s_nbig = 0;
         }
+        __syncthreads();
+        const uint32_t base = s_base;
+        uint32_t* nq = s_q[cur ^ 1];
+        uint32_t* nqn = &s_qn[cur ^ 1];
+        for (uint32_t i = warp; i < cnt; i += nwarps) {
+          const uint32_t v = s_q[cur][i];
+          if (lane == 0) {
+            a.rank[v] = base + i;
+            a.vert[base + i] = v;
+          }
+          const uint64_t b = a.rowptr[v], e = a.rowptr[v + 1];
+          if (e - b > kPeelBig) {
+            uint32_t slot = 0;
+            if (lane == 0) slot = atomicAdd(&s_nbig, 1u);
+            slot = __shfl_sync(0xFFFFFFFFu, slot, 0);
+            if (slot < kPeelBigMax) {
+              if (lane == 0) s_big[slot] = v;
+              continue;
+            }
+          }
+          peel_edges(a, b, e, lane, 32, k, nq, nqn, spill, spill_cnt);
+        }
+        __syncthreads();
+        // high-degree vertices of this wave: the whole block strides over each edge list
+        const uint32_t nbig = min(s_nbig, kPeelBigMax);
+        for (uint32_t j = 0; j < nbig; j++) {
+          const uint32_t v = s_big[j];
+          peel_edges(a, a.rowptr[v], a.rowptr[v + 1], tid, blockDim.x, k, nq, nqn, spill, spill_cnt);
+        }
+        cur ^= 1;
       }
+      if (!grid_barrier(&a.bar[0], &a.bar[1], nb, a.spin_limit, a.status)) return;
+      const uint32_t spilled = vctr[sub % 3];
+      removed += vctr[4 + sub % 3];
+      sub++;
+      first = false;
+      if (spilled == 0) break;
     }
-    if (!grid_barrier(&a.bar[0], &a.bar[1], nb, a.spin_limit, a.status)) return;
-    uint32_t* t = alive;
-    alive = alive_next;
-    alive_next = t;
-    na -= F;
-    next_rank += F;
-    round++;
+    if (removed > removed0) degen = k;
+    k++;
   }
-  if (bid == 0 && threadIdx.x == 0) {
-    // k only rises to a level where someone is removed, so it ends at the max core.
-    a.result[0] = k;
-    a.result[1] = round;
+  if (bid == 0 && tid == 0) {
+    a.result[0] = degen;
+    a.result[1] = sub;
   }
 }
 
@@ -776,8 +819,8 @@ int prep_graph(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr_in, const uint32_
     uint64_t need_blocks = ((uint64_t)n + kPeelThreads - 1) / kPeelThreads;
     nb = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(nb, need_blocks));
     uint32_t* pw = nullptr;
-    KC_TRY(scratch_get(ctx, kScrPeel, (4ull * nb + 16) * sizeof(uint32_t), (void**)&pw));
-    KC_CUDA(cudaMemsetAsync(pw, 0, (4ull * nb + 16) * sizeof(uint32_t), s));
+    KC_TRY(scratch_get(ctx, kScrPeel, 16 * sizeof(uint32_t), (void**)&pw));
+    KC_CUDA(cudaMemsetAsync(pw, 0, 16 * sizeof(uint32_t), s));
     PeelArgs pa;
     pa.rowptr = rowptr;
     pa.col = col;
@@ -786,12 +829,10 @@ int prep_graph(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr_in, const uint32_
     pa.core = g->core;
     pa.rank = g->rank;
     pa.vert = g->vert;
-    pa.alive0 = alive0;
-    pa.alive1 = alive1;
-    pa.frontier = frontier;
-    pa.blkcnt = pw;
-    pa.minrem = pw + 4 * nb;
-    pa.bar = pw + 4 * nb + 4;
+    pa.spill0 = alive0;
+    pa.spill1 = alive1;
+    pa.ctr = pw;
+    pa.bar = pw + 8;
     pa.status = d_status;
     pa.result = d_peelres;
     pa.spin_limit = ctx->opts.spin_limit;

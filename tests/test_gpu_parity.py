@@ -241,6 +241,12 @@ def test_split_path_matches_oracle(maker, splits):
     lambda: gg.chung_lu_planted(n=20000, n_cliques=40, seed=1),
     lambda: gg.complete(70),
     lambda: gg.rgg_torus(5000, 30.0, seed=5),
+    # two million low-degree vertices: every block's first wave outgrows shared memory and spills
+    lambda: gg.er_gnm(2_000_000, 3_000_000, seed=9),
+    # a perfect matching on two million vertices: the level-1 scan of every block spills
+    lambda: gg.csr_from_pairs(2_000_000, np.arange(0, 2_000_000, 2), np.arange(1, 2_000_000, 2)),
+    # a long path: one removal cascade of 50,000 waves
+    lambda: gg.csr_from_pairs(100_000, np.arange(99_999), np.arange(1, 100_000)),
 ])
 def test_core_numbers_and_dag(ctx, maker):
     g = maker()

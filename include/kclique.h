@@ -176,6 +176,20 @@ int kc_list_range(kc_ctx* ctx, kc_graph g, uint32_t k, uint32_t root_lo, uint32_
                   uint64_t cap, uint64_t* written, uint64_t* total, uint64_t* checksum, void* stream);
 
 /*
+ * Batched counting: counts[i] (host) = the number of ks[i]-cliques of the
+ * resident graph graphs[i], for i < nq.  Graphs may repeat, with the same or
+ * different k.  The roots of every query (one NodeParallel subtask per root,
+ * Sec. VII-D) are binned together by bitmap width and enumerated by one set
+ * of tier launches -- the same kernels as kc_count, each warp binding the
+ * query of the root it takes -- instead of one set of launches per graph.
+ * Results equal nq separate kc_count calls.  Errors: KC_E_INVALID_ARG (NULL
+ * array with nq > 0, a k of 0), KC_E_NOT_FOUND (unknown graph),
+ * KC_E_UNSUPPORTED (k > KC_MAX_K).  Synchronises the stream.
+ */
+int kc_count_batched(kc_ctx* ctx, const kc_graph* graphs, const uint32_t* ks, uint32_t nq, uint64_t* counts,
+                     void* stream);
+
+/*
  * Count the k-cliques of a DAG that is already in device memory, without
  * allocating any memory.  The paper has no counterpart: this entry point is
  * for callers that cannot call cudaMalloc (or any allocator) when they

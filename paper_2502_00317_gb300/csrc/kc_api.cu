@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "kc_internal.cuh"
 
@@ -286,6 +287,37 @@ int kc_list_range(kc_ctx* ctx, kc_graph h, uint32_t k, uint32_t root_lo, uint32_
   if (cap > 0 && !d_buf) return KC_E_INVALID_ARG;
   if (root_lo > root_hi) return KC_E_INVALID_ARG;
   return enum_common(ctx, h, k, 1, root_lo, root_hi, d_buf, cap, written, total, checksum, stream);
+}
+
+int kc_count_batched(kc_ctx* ctx, const kc_graph* graphs, const uint32_t* ks, uint32_t nq, uint64_t* counts,
+                     void* stream) {
+  if (!ctx || (nq > 0 && (!graphs || !ks || !counts))) return KC_E_INVALID_ARG;
+  std::vector<BatchQuery> q(nq);
+  for (uint32_t i = 0; i < nq; i++) {
+    auto it = ctx->graphs.find(graphs[i]);
+    if (it == ctx->graphs.end()) return KC_E_NOT_FOUND;
+    const uint32_t k = ks[i];
+    if (k == 0) return KC_E_INVALID_ARG;
+    if (k > KC_MAX_K) return KC_E_UNSUPPORTED;
+  }
+  for (uint32_t i = 0; i < nq; i++) {
+    const DevGraph& g = ctx->graphs.find(graphs[i])->second;
+    const uint32_t k = ks[i];
+    q[i] = BatchQuery{g.orow, g.ocol, g.vert, g.n, k};
+    counts[i] = 0;
+    if (k == 1) counts[i] = g.n;
+    if (k == 2) counts[i] = g.m;
+    // k <= 2, or no root with k-1 out-neighbours: answered here
+    if (k <= 2 || (uint64_t)k - 1 > g.max_out) q[i].n = 0;
+  }
+  KC_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = pick_stream(ctx, stream);
+  ctx->last = kc_stats{};
+  std::vector<uint64_t> got(std::max<uint32_t>(nq, 1), 0);
+  KC_TRY(run_batch(ctx, q.data(), nq, ctx->opts.no_memo == 0, ctx->opts.no_prune == 0, got.data(), s));
+  for (uint32_t i = 0; i < nq; i++)
+    if (q[i].n) counts[i] = got[i];
+  return KC_OK;
 }
 
 int kc_last_stats(kc_ctx* ctx, kc_stats* out) {

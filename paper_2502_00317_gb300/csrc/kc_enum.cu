@@ -27,6 +27,7 @@
 //          frame every frame is memoised, as Algorithm 3 recurses into itself.
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "kc_internal.cuh"
 
@@ -64,7 +65,13 @@ struct EnumKArgs {
   unsigned long long task_cap;
   unsigned long long* task_used;
   unsigned long long* task_head;
+  // batched counting: per-query graph and k, the query of each root, counts
+  const BatchQuery* bq;         // nullptr: one graph (the fields above)
+  const uint32_t* roots_q;      // [nroots] query of each root
+  unsigned long long* bcount;   // [queries] counts
+  uint32_t query;               // query bound to this copy of the arguments
 };
+
 
 // Per-warp working state, carved from shared or global memory.
 template <int W>
@@ -903,6 +910,7 @@ __device__ bool publish_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, i
   if (lane == 0) {
     hdr[0] = u;
     hdr[1] = (uint32_t)d;
+    hdr[2] = a.query;
   }
   for (int i = lane; i < d; i += 32) {
     nbr[i] = st.nbr[i];
@@ -1002,13 +1010,96 @@ __device__ __forceinline__ void next_epoch(Memo& memo, uint32_t* epoch) {
 
 // Phase 1: one warp per root, roots taken from the tier's list.
 // MODE 0: count (plain), 1: list, 2: count with memo.
+// Everything for one root u of the graph in `a`: build, prune, then split,
+// count or list.  Counts accumulate in acc.cnt (lane-partial).
+template <int W, int MODE>
+__device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint32_t* epoch, uint32_t u, Acc& acc) {
+  const uint32_t lane = lane_id();
+  const uint32_t need = a.k - 1;
+  const int d = (int)(a.orow[u + 1] - a.orow[u]);
+  if (!build_root<W>(st, a, u, d, acc)) return;
+  uint32_t S0[W];
+  all_bits<W>(d, S0);
+  if (MODE == 2) next_epoch(memo, epoch);
+  // Eq. (1) on G_u for the root frame
+  bool dense0 = false;
+  if (MODE == 2 && a.memo && need > 3) {
+    uint32_t er = 0;
+    for (int i = lane; i < d * W; i += 32) er += __popc(st.rows[i]);
+    er = warp_sum(er);
+    dense0 = 2ull * need * er > (unsigned long long)(need - 1) * d * d;
+  }
+  // heavy roots go to the split path: one task per first-level branch
+  // dense roots keep their memo whole unless they are wide (more than 64 out-neighbours)
+  if (a.split_wedges && d > a.split_min_d && (!dense0 || W >= 4) && need >= 4) {
+    uint32_t wg = 0;
+    for (int i = lane; i < d; i += 32) {
+      uint32_t p = 0;
+#pragma unroll
+      for (int w = 0; w < W; w++) p += __popc(st.rows[(size_t)i * W + w]);
+      wg += p * (p - 1) / 2;
+    }
+    wg = warp_sum(wg);
+    // a wide dense root's search grows with k: its threshold halves for every k above 5
+    const uint32_t thr = dense0 ? (a.split_wedges >> min(need - 4u, 12u)) : a.split_wedges;
+    if (wg > thr && publish_root<W, MODE>(st, a, u, d, acc)) return;
+  }
+  if (MODE != 1 && need >= 2 && need <= kCompactMaxL && d <= 32 && !dense0) {
+    // the whole root at once: one word per row, lanes take the smallest vertex
+    acc.cnt += count_compact<W>(st, S0, (uint32_t)d, need, acc.ops);
+  } else if (MODE == 0 || MODE == 1) {
+    if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
+    if (lane == 0) {
+      st.pos[0] = d - 1;
+      if (MODE == 1) st.sid[0] = a.vert[u];
+    }
+    __syncwarp();
+    dfs_plain<W, MODE>(st, a, 0, acc);
+  } else {
+    if (need <= 3) {
+      unsigned long long v = small_count<W>(st, S0, need, acc);
+      if (lane == 0) acc.cnt += v;
+    } else {
+      if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
+      if (lane == 0) {
+        st.pos[0] = d - 1;
+        st.sum[0] = 0;
+        st.dense[0] = dense0;
+        st.fullins[0] = 0;
+      }
+      __syncwarp();
+      unsigned long long v = dfs_memo<W>(st, a, memo, 0, acc);
+      if (lane == 0) acc.cnt += v;
+    }
+  }
+}
+
+// The graph and k of batch query q (batched counting).
+__device__ __forceinline__ void bind_query(EnumKArgs& b, const EnumKArgs& a, uint32_t q) {
+  const BatchQuery bq = a.bq[q];
+  b.orow = bq.orow;
+  b.ocol = bq.ocol;
+  b.vert = bq.vert;
+  b.k = bq.k;
+  b.query = q;
+}
+
+// A batch query's count so far, moved from the lanes' partials to its slot.
+__device__ __forceinline__ void flush_query(const EnumKArgs& a, uint32_t q, Acc& acc) {
+  const unsigned long long c = warp_sum(acc.cnt);
+  acc.cnt = 0;
+  if (lane_id() == 0 && c) atomicAdd(&a.bcount[q], c);
+}
+
+// Phase 1: one warp per root, roots taken from the tier's list.  With a batch
+// (a.bq set) each list entry also names its query.
+// MODE 0: count (plain), 1: list, 2: count with memo.
 template <int W, int MODE>
 __global__ void __launch_bounds__(256) k_enum(EnumKArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = lane_id();
   WarpState<W> st;
   carve_state<W>(st, a, smem);
-  const uint32_t need = a.k - 1;
   Acc acc;
   Memo memo = warp_memo<W>(a);
   uint32_t epoch = 0;
@@ -1018,61 +1109,14 @@ __global__ void __launch_bounds__(256) k_enum(EnumKArgs a) {
     qi = __shfl_sync(0xFFFFFFFFu, qi, 0);
     if (qi >= a.nroots) break;
     const uint32_t u = a.roots[qi];
-    const int d = (int)(a.orow[u + 1] - a.orow[u]);
-    if (!build_root<W>(st, a, u, d, acc)) continue;
-    uint32_t S0[W];
-    all_bits<W>(d, S0);
-    if (MODE == 2) next_epoch(memo, &epoch);
-    // Eq. (1) on G_u for the root frame
-    bool dense0 = false;
-    if (MODE == 2 && a.memo && need > 3) {
-      uint32_t er = 0;
-      for (int i = lane; i < d * W; i += 32) er += __popc(st.rows[i]);
-      er = warp_sum(er);
-      dense0 = 2ull * need * er > (unsigned long long)(need - 1) * d * d;
-    }
-    // heavy roots go to the split path: one task per first-level branch
-    // dense roots keep their memo whole unless they are wide (more than 64 out-neighbours)
-    if (a.split_wedges && d > a.split_min_d && (!dense0 || W >= 4) && need >= 4) {
-      uint32_t wg = 0;
-      for (int i = lane; i < d; i += 32) {
-        uint32_t p = 0;
-#pragma unroll
-        for (int w = 0; w < W; w++) p += __popc(st.rows[(size_t)i * W + w]);
-        wg += p * (p - 1) / 2;
-      }
-      wg = warp_sum(wg);
-      // a wide dense root's search grows with k: its threshold halves for every k above 5
-      const uint32_t thr = dense0 ? (a.split_wedges >> min(need - 4u, 12u)) : a.split_wedges;
-      if (wg > thr && publish_root<W, MODE>(st, a, u, d, acc)) continue;
-    }
-    if (MODE != 1 && need >= 2 && need <= kCompactMaxL && d <= 32 && !dense0) {
-      // the whole root at once: one word per row, lanes take the smallest vertex
-      acc.cnt += count_compact<W>(st, S0, (uint32_t)d, need, acc.ops);
-    } else if (MODE == 0 || MODE == 1) {
-      if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
-      if (lane == 0) {
-        st.pos[0] = d - 1;
-        st.sid[0] = a.vert[u];
-      }
-      __syncwarp();
-      dfs_plain<W, MODE>(st, a, 0, acc);
+    if (MODE != 1 && a.bq) {
+      const uint32_t q = a.roots_q[qi];
+      EnumKArgs b = a;
+      bind_query(b, a, q);
+      root_body<W, MODE>(st, b, memo, &epoch, u, acc);
+      flush_query(a, q, acc);
     } else {
-      if (need <= 3) {
-        unsigned long long v = small_count<W>(st, S0, need, acc);
-        if (lane == 0) acc.cnt += v;
-      } else {
-        if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
-        if (lane == 0) {
-          st.pos[0] = d - 1;
-          st.sum[0] = 0;
-          st.dense[0] = dense0;
-          st.fullins[0] = 0;
-        }
-        __syncwarp();
-        unsigned long long v = dfs_memo<W>(st, a, memo, 0, acc);
-        if (lane == 0) acc.cnt += v;
-      }
+      root_body<W, MODE>(st, a, memo, &epoch, u, acc);
     }
     acc.ops64 += acc.ops;
     acc.ops = 0;
@@ -1089,7 +1133,8 @@ __global__ void __launch_bounds__(256) k_tasks(EnumKArgs a) {
   const uint32_t lane = lane_id();
   WarpState<W> st;
   carve_state<W>(st, a, smem);
-  const uint32_t need = a.k - 1;
+  EnumKArgs b = a;  // bound to the current root's query in a batch
+  uint32_t need = a.k - 1;
   Acc acc;
   Memo memo = warp_memo<W>(a);
   uint32_t epoch = 1u << 24;  // above every epoch of phase 1
@@ -1110,6 +1155,10 @@ __global__ void __launch_bounds__(256) k_tasks(EnumKArgs a) {
       const uint32_t* hdr = (const uint32_t*)base;
       u = hdr[0];
       d = (int)hdr[1];
+      if (MODE != 1 && a.bq) {
+        bind_query(b, a, hdr[2]);
+        need = b.k - 1;
+      }
       const uint32_t* nbr = hdr + 4;
       const uint32_t* rows = nbr + d;
       const uint8_t* rr = (const uint8_t*)(rows + (size_t)d * W);
@@ -1132,7 +1181,8 @@ __global__ void __launch_bounds__(256) k_tasks(EnumKArgs a) {
       cur = off;
       if (MODE == 2) next_epoch(memo, &epoch);
     }
-    run_branch<W, MODE>(st, a, memo, u, d, v1, acc);
+    run_branch<W, MODE>(st, b, memo, u, d, v1, acc);
+    if (MODE != 1 && a.bq) flush_query(a, b.query, acc);
     acc.ops64 += acc.ops;
     acc.ops = 0;
     __syncwarp();
@@ -1273,6 +1323,90 @@ static int plan_all(kc_ctx* ctx, const uint32_t* hcnt, bool split, TierPlan* pla
 // its G_u (sum over local vertices of C(out-degree, 2)) exceeds this.
 constexpr uint32_t kDefaultSplitWedges = 16384;
 
+// Plans and launches the enumerator of every non-empty width tier, each on
+// its own stream (widest first), joined back into `s`.  troots[t] lists the
+// tier's roots (troots_q[t] their queries in a batch, else nullptr).
+static int launch_tiers(kc_ctx* ctx, const EnumKArgs& args, const uint32_t* hcnt, uint32_t* const* troots,
+                        uint32_t* const* troots_q, int mode, bool split_ok, cudaStream_t s, uint32_t* launches,
+                        uint32_t* enum_launches) {
+  const uint32_t split_wedges =
+      ctx->opts.split_threshold == 0 ? kDefaultSplitWedges
+      : (ctx->opts.split_threshold == 0xFFFFFFFFu ? 0u : ctx->opts.split_threshold);
+  // the split path needs at least two levels below the first branch (k >= 5)
+  const bool split = split_wedges != 0 && split_ok;
+  TierPlan plans[kTiers];
+  if (mode == 1) KC_TRY(plan_all<1>(ctx, hcnt, split, plans));
+  else if (mode == 2) KC_TRY(plan_all<2>(ctx, hcnt, split, plans));
+  else KC_TRY(plan_all<0>(ctx, hcnt, split, plans));
+  // one scratch region for every tier's global state, memo tables, arena and task queue
+  uint64_t total = 0;
+  uint64_t goff[kTiers], moff[kTiers], aoff[kTiers], toff[kTiers];
+  for (int t = 0; t < kTiers; t++) {
+    goff[t] = total;
+    total += (plans[t].gstate_bytes * plans[t].blocks * std::max(plans[t].warps_per_block, 1) + 255) & ~255ull;
+    moff[t] = total;
+    total += (plans[t].memo_bytes + 255) & ~255ull;
+    aoff[t] = total;
+    total += (plans[t].arena_units * 16 + 255) & ~255ull;
+    toff[t] = total;
+    total += (plans[t].task_cap * 8 + 255) & ~255ull;
+  }
+  void* base = nullptr;
+  if (total) KC_TRY(scratch_get(ctx, kScrEnum, total, &base));
+  KC_CUDA(cudaEventRecord(ctx->ev_fork, s));
+  for (int t = kTiers - 1; t >= 0; t--) {
+    const TierPlan& tp = plans[t];
+    if (tp.nroots == 0) continue;
+    cudaStream_t ts = ctx->tier_stream[t];
+    KC_CUDA(cudaStreamWaitEvent(ts, ctx->ev_fork, 0));
+    EnumKArgs x = args;
+    x.roots = troots[t];
+    x.roots_q = troots_q ? troots_q[t] : nullptr;
+    x.nroots = tp.nroots;
+    x.qctr = (unsigned int*)&ctx->d_acc[kAccQueue0 + t];
+    if (tp.gstate_bytes) {
+      x.gstate = (uint8_t*)base + goff[t];
+      x.gstride = tp.gstate_bytes;
+    }
+    if (tp.memo_cap) {
+      uint64_t warps = tp.blocks * tp.warps_per_block;
+      uint8_t* mb = (uint8_t*)base + moff[t];
+      x.memo_vals = (unsigned long long*)mb;
+      x.memo_tags = (uint32_t*)(mb + warps * tp.memo_cap * 8);
+      x.memo_keys = (uint32_t*)(mb + warps * tp.memo_cap * 12);
+      x.memo_cap = tp.memo_cap;
+      KC_CUDA(cudaMemsetAsync(x.memo_tags, 0, warps * tp.memo_cap * 4, ts));
+    }
+    if (tp.split) {
+      x.split_wedges = split_wedges;
+      x.split_min_d = 32;
+      x.arena = (uint8_t*)base + aoff[t];
+      x.arena_units = tp.arena_units;
+      x.arena_used = &ctx->d_acc[kAccArena0 + t];
+      x.tasks = (unsigned long long*)((uint8_t*)base + toff[t]);
+      x.task_cap = tp.task_cap;
+      x.task_used = &ctx->d_acc[kAccTaskUsed0 + t];
+      x.task_head = &ctx->d_acc[kAccTaskHead0 + t];
+    }
+    void* kargs[] = {&x};
+    KC_CUDA(cudaEventRecord(ctx->ev_tier0[t], ts));
+    KC_CUDA(cudaLaunchKernel(tp.fn, dim3((unsigned)tp.blocks), dim3(tp.warps_per_block * 32), kargs, tp.smem, ts));
+    (*launches)++;
+    (*enum_launches)++;
+    if (tp.split) {
+      // second phase: (root, first-level branch) tasks of the roots the first phase published
+      KC_CUDA(cudaLaunchKernel(tp.fn_tasks, dim3((unsigned)tp.blocks), dim3(tp.warps_per_block * 32), kargs, tp.smem,
+                               ts));
+      (*launches)++;
+      (*enum_launches)++;
+    }
+    KC_CUDA(cudaEventRecord(ctx->ev_tier1[t], ts));
+    KC_CUDA(cudaEventRecord(ctx->ev_join[t], ts));
+    KC_CUDA(cudaStreamWaitEvent(s, ctx->ev_join[t], 0));
+  }
+  return KC_OK;
+}
+
 int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s) {
   kc_stats stt{};
   uint32_t launches = 0, enum_launches = 0;
@@ -1312,30 +1446,6 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
     if (hcnt[kTiers] != 0) return KC_E_UNSUPPORTED;  // out-degree above the widest tier
     // memo needs at least one level to split (k >= 3); k = 2 counts by popcount
     const int mode = ea.mode == 1 ? 1 : ((ea.memo && k >= 3) ? 2 : 0);
-    const uint32_t split_wedges =
-        ctx->opts.split_threshold == 0 ? kDefaultSplitWedges
-        : (ctx->opts.split_threshold == 0xFFFFFFFFu ? 0u : ctx->opts.split_threshold);
-    // the split path needs at least two levels below the first branch
-    const bool split = split_wedges != 0 && k >= 5;
-    TierPlan plans[kTiers];
-    if (mode == 1) KC_TRY(plan_all<1>(ctx, hcnt, split, plans));
-    else if (mode == 2) KC_TRY(plan_all<2>(ctx, hcnt, split, plans));
-    else KC_TRY(plan_all<0>(ctx, hcnt, split, plans));
-    // one scratch region for every tier's global state, memo tables, arena and task queue
-    uint64_t total = 0;
-    uint64_t goff[kTiers], moff[kTiers], aoff[kTiers], toff[kTiers];
-    for (int t = 0; t < kTiers; t++) {
-      goff[t] = total;
-      total += (plans[t].gstate_bytes * plans[t].blocks * std::max(plans[t].warps_per_block, 1) + 255) & ~255ull;
-      moff[t] = total;
-      total += (plans[t].memo_bytes + 255) & ~255ull;
-      aoff[t] = total;
-      total += (plans[t].arena_units * 16 + 255) & ~255ull;
-      toff[t] = total;
-      total += (plans[t].task_cap * 8 + 255) & ~255ull;
-    }
-    void* base = nullptr;
-    if (total) KC_TRY(scratch_get(ctx, kScrEnum, total, &base));
     EnumKArgs args{};
     args.orow = g.orow;
     args.ocol = g.ocol;
@@ -1347,57 +1457,9 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
     args.cap = ea.cap;
     args.acc = ctx->d_acc;
     args.status = ctx->d_status;
-    // fork: every non-empty tier on its own stream, widest first
-    KC_CUDA(cudaEventRecord(ctx->ev_fork, s));
-    for (int t = kTiers - 1; t >= 0; t--) {
-      const TierPlan& tp = plans[t];
-      if (tp.nroots == 0) continue;
-      cudaStream_t ts = ctx->tier_stream[t];
-      KC_CUDA(cudaStreamWaitEvent(ts, ctx->ev_fork, 0));
-      EnumKArgs x = args;
-      x.roots = lists + (size_t)t * lcap;
-      x.nroots = tp.nroots;
-      x.qctr = (unsigned int*)&ctx->d_acc[kAccQueue0 + t];
-      if (tp.gstate_bytes) {
-        x.gstate = (uint8_t*)base + goff[t];
-        x.gstride = tp.gstate_bytes;
-      }
-      if (tp.memo_cap) {
-        uint64_t warps = tp.blocks * tp.warps_per_block;
-        uint8_t* mb = (uint8_t*)base + moff[t];
-        x.memo_vals = (unsigned long long*)mb;
-        x.memo_tags = (uint32_t*)(mb + warps * tp.memo_cap * 8);
-        x.memo_keys = (uint32_t*)(mb + warps * tp.memo_cap * 12);
-        x.memo_cap = tp.memo_cap;
-        KC_CUDA(cudaMemsetAsync(x.memo_tags, 0, warps * tp.memo_cap * 4, ts));
-      }
-      if (tp.split) {
-        x.split_wedges = split_wedges;
-        x.split_min_d = 32;
-        x.arena = (uint8_t*)base + aoff[t];
-        x.arena_units = tp.arena_units;
-        x.arena_used = &ctx->d_acc[kAccArena0 + t];
-        x.tasks = (unsigned long long*)((uint8_t*)base + toff[t]);
-        x.task_cap = tp.task_cap;
-        x.task_used = &ctx->d_acc[kAccTaskUsed0 + t];
-        x.task_head = &ctx->d_acc[kAccTaskHead0 + t];
-      }
-      void* kargs[] = {&x};
-      KC_CUDA(cudaEventRecord(ctx->ev_tier0[t], ts));
-      KC_CUDA(cudaLaunchKernel(tp.fn, dim3((unsigned)tp.blocks), dim3(tp.warps_per_block * 32), kargs, tp.smem, ts));
-      launches++;
-      enum_launches++;
-      if (tp.split) {
-        // second phase: (root, first-level branch) tasks of the roots the first phase published
-        KC_CUDA(cudaLaunchKernel(tp.fn_tasks, dim3((unsigned)tp.blocks), dim3(tp.warps_per_block * 32), kargs, tp.smem,
-                                 ts));
-        launches++;
-        enum_launches++;
-      }
-      KC_CUDA(cudaEventRecord(ctx->ev_tier1[t], ts));
-      KC_CUDA(cudaEventRecord(ctx->ev_join[t], ts));
-      KC_CUDA(cudaStreamWaitEvent(s, ctx->ev_join[t], 0));
-    }
+    uint32_t* troots[kTiers];
+    for (int t = 0; t < kTiers; t++) troots[t] = lists + (size_t)t * lcap;
+    KC_TRY(launch_tiers(ctx, args, hcnt, troots, nullptr, mode, k >= 5, s, &launches, &enum_launches));
     for (int t = 0; t < kTiers; t++) tier_roots[t] = hcnt[t];
     KC_CUDA(cudaEventRecord(ev[7], s));
   }
@@ -1424,6 +1486,174 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
       stt.ms_tier[t] = 0.f;
       if (tier_roots[t]) cudaEventElapsedTime(&stt.ms_tier[t], ctx->ev_tier0[t], ctx->ev_tier1[t]);
     }
+  }
+  ctx->last = stt;
+  return KC_OK;
+}
+
+
+// ------------------------------------------------------------ batched count
+// Roots of every query of a batch, binned by width: the flattened index g over
+// all queries' ranks maps to (query, rank) by a binary search of the query
+// offsets.  Pass 0 counts the roots of each tier, pass 1 writes them at the
+// tier's offset (tier_off), warp-aggregated.
+struct BinBatchArgs {
+  const BatchQuery* bq;
+  const uint64_t* qoff;  // [nq + 1] running sum of the queries' n
+  uint32_t nq;
+  uint64_t total;
+  uint32_t* cnts;        // [16]: per-tier counts (pass 0) or cursors (pass 1); [kTiers] too wide
+  uint32_t tier_off[kTiers];
+  uint32_t* roots;
+  uint32_t* roots_q;
+  unsigned long long* acc;
+  int pass;
+};
+
+__global__ void k_bin_batch(BinBatchArgs a) {
+  const uint32_t lane = lane_id();
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long tot = 0;
+  for (uint64_t w0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5; w0 < a.total; w0 += nw << 5) {
+    const uint64_t g = w0 + lane;
+    uint32_t t = 0xFFu, q = 0, r = 0;
+    if (g < a.total) {
+      uint32_t lo = 0, hi = a.nq;  // last query whose offset is <= g
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a.qoff[mid] <= g) lo = mid;
+        else hi = mid;
+      }
+      q = lo;
+      r = (uint32_t)(g - a.qoff[q]);
+      const BatchQuery bq = a.bq[q];
+      const uint32_t d = (uint32_t)(bq.orow[r + 1] - bq.orow[r]);
+      if (bq.k >= 3 && d >= bq.k - 1) {
+        const uint32_t words = (d + 31) >> 5;
+        t = 0;
+        while (t < (uint32_t)kTiers && (uint32_t)tier_words((int)t) < words) t++;
+        tot++;
+      }
+    }
+    const uint32_t same = __match_any_sync(0xFFFFFFFFu, t);
+    const uint32_t leader = __ffs(same) - 1;
+    uint32_t basep = 0;
+    if (lane == leader && t != 0xFFu) basep = atomicAdd(&a.cnts[t], (uint32_t)__popc(same));
+    basep = __shfl_sync(0xFFFFFFFFu, basep, leader);
+    if (a.pass == 1 && t < (uint32_t)kTiers) {
+      const uint32_t pos = a.tier_off[t] + basep + __popc(same & lanemask_lt());
+      a.roots[pos] = r;
+      a.roots_q[pos] = q;
+    }
+  }
+  tot = warp_sum(tot);
+  if (a.pass == 0 && lane == 0 && tot) atomicAdd(&a.acc[kAccRootsTotal], tot);
+}
+
+int run_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, bool memo, bool prune, uint64_t* counts,
+              cudaStream_t s) {
+  kc_stats stt{};
+  uint32_t launches = 0, enum_launches = 0;
+  cudaEvent_t* ev = ctx->ev;
+  KC_CUDA(cudaEventRecord(ev[5], s));
+  KC_CUDA(cudaMemsetAsync(ctx->d_acc, 0, kAccSlots * sizeof(unsigned long long), s));
+  std::vector<uint64_t> qoff(nq + 1, 0);
+  bool any5 = false;
+  for (uint32_t q = 0; q < nq; q++) {
+    qoff[q + 1] = qoff[q] + hq[q].n;
+    any5 |= hq[q].k >= 5;
+  }
+  const uint64_t total = qoff[nq];
+  // device copies of the queries, offsets, counts and tier counters
+  const size_t qbytes = ((size_t)nq * sizeof(BatchQuery) + 255) & ~(size_t)255;
+  const size_t obytes = (((size_t)nq + 1) * 8 + 255) & ~(size_t)255;
+  const size_t cbytes = ((size_t)nq * 8 + 255) & ~(size_t)255;
+  void* meta = nullptr;
+  KC_TRY(scratch_get(ctx, kScrBatch, qbytes + obytes + cbytes + 256, &meta));
+  BatchQuery* d_q = (BatchQuery*)meta;
+  uint64_t* d_off = (uint64_t*)((uint8_t*)meta + qbytes);
+  unsigned long long* d_cnt = (unsigned long long*)((uint8_t*)meta + qbytes + obytes);
+  uint32_t* d_tc = (uint32_t*)((uint8_t*)meta + qbytes + obytes + cbytes);
+  KC_CUDA(cudaMemcpyAsync(d_q, hq, (size_t)nq * sizeof(BatchQuery), cudaMemcpyHostToDevice, s));
+  KC_CUDA(cudaMemcpyAsync(d_off, qoff.data(), ((size_t)nq + 1) * 8, cudaMemcpyHostToDevice, s));
+  KC_CUDA(cudaMemsetAsync(d_cnt, 0, (size_t)nq * 8, s));
+  KC_CUDA(cudaMemsetAsync(d_tc, 0, 256, s));
+  BinBatchArgs ba{};
+  ba.bq = d_q;
+  ba.qoff = d_off;
+  ba.nq = nq;
+  ba.total = total;
+  ba.cnts = d_tc;
+  ba.acc = ctx->d_acc;
+  const unsigned bb =
+      (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->num_sms * 8));
+  uint32_t hcnt[16] = {0};
+  if (total) {
+    ba.pass = 0;
+    k_bin_batch<<<bb, 256, 0, s>>>(ba);
+    KC_CUDA(cudaGetLastError());
+    launches++;
+    KC_CUDA(cudaMemcpyAsync(hcnt, d_tc, sizeof(hcnt), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+  }
+  if (hcnt[kTiers] != 0) return KC_E_UNSUPPORTED;  // out-degree above the widest tier
+  uint64_t nroots = 0;
+  for (int t = 0; t < kTiers; t++) {
+    ba.tier_off[t] = (uint32_t)nroots;
+    nroots += hcnt[t];
+  }
+  if (nroots >= (1ull << 32)) return KC_E_UNSUPPORTED;
+  void* lp = nullptr;
+  KC_TRY(scratch_get(ctx, kScrRoots, (2 * std::max<uint64_t>(nroots, 1) + 16) * sizeof(uint32_t), &lp));
+  ba.roots = (uint32_t*)lp;
+  ba.roots_q = ba.roots + std::max<uint64_t>(nroots, 1);
+  if (nroots) {
+    KC_CUDA(cudaMemsetAsync(d_tc, 0, 64, s));
+    ba.pass = 1;
+    k_bin_batch<<<bb, 256, 0, s>>>(ba);
+    KC_CUDA(cudaGetLastError());
+    launches++;
+  }
+  KC_CUDA(cudaEventRecord(ev[6], s));
+  if (nroots) {
+    EnumKArgs args{};
+    args.k = 3;  // per query through bq; this value is never used for a root
+    args.prune = prune ? 1 : 0;
+    args.memo = memo ? 1 : 0;
+    args.acc = ctx->d_acc;
+    args.status = ctx->d_status;
+    args.bq = d_q;
+    args.bcount = d_cnt;
+    uint32_t* troots[kTiers];
+    uint32_t* troots_q[kTiers];
+    for (int t = 0; t < kTiers; t++) {
+      troots[t] = ba.roots + ba.tier_off[t];
+      troots_q[t] = ba.roots_q + ba.tier_off[t];
+    }
+    KC_TRY(launch_tiers(ctx, args, hcnt, troots, troots_q, memo ? 2 : 0, any5, s, &launches, &enum_launches));
+  }
+  KC_CUDA(cudaEventRecord(ev[7], s));
+  KC_CUDA(cudaMemcpyAsync(counts, d_cnt, (size_t)nq * 8, cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc, kAccSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaEventRecord(ev[8], s));
+  KC_CUDA(cudaEventSynchronize(ev[8]));
+  cudaEventElapsedTime(&stt.ms_bin, ev[5], ev[6]);
+  cudaEventElapsedTime(&stt.ms_enum, ev[6], ev[7]);
+  cudaEventElapsedTime(&stt.ms_total, ev[5], ev[8]);
+  stt.enum_launches = enum_launches;
+  stt.total_launches = launches;
+  stt.roots_total = ctx->h_acc[kAccRootsTotal];
+  stt.roots_pruned = ctx->h_acc[kAccRootsPruned];
+  stt.roots_heavy = ctx->h_acc[kAccRootsHeavy];
+  stt.build_words = ctx->h_acc[kAccBuildWords];
+  stt.memo_hits = ctx->h_acc[kAccMemoHits];
+  stt.memo_inserts = ctx->h_acc[kAccMemoInserts];
+  stt.memo_full = ctx->h_acc[kAccMemoFull];
+  stt.memo_frames = ctx->h_acc[kAccMemoFrames];
+  stt.word_ops = ctx->h_acc[kAccWordOps];
+  for (int t = 0; t < kTiers; t++) {
+    stt.roots_tier[t] = hcnt[t];
+    if (hcnt[t]) cudaEventElapsedTime(&stt.ms_tier[t], ctx->ev_tier0[t], ctx->ev_tier1[t]);
   }
   ctx->last = stt;
   return KC_OK;

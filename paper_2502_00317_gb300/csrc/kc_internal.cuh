@@ -166,7 +166,7 @@ enum AccSlot : int {
 // Scratch slots.
 enum ScratchSlot : int {
   kScrA = 0, kScrB, kScrC, kScrD, kScrE, kScrF, kScrG, kScrScan, kScrSort, kScrSortList, kScrEnum, kScrMemo,
-  kScrRoots, kScrPeel, kScrSplit,
+  kScrRoots, kScrPeel, kScrSplit, kScrBatch,
   kScrSlots
 };
 
@@ -210,5 +210,17 @@ struct EnumArgs {
   bool prune = true;
 };
 int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& a, cudaStream_t s);
+
+// Batched counting (kc_enum.cu): one query per (graph, k); every query with
+// n > 0 and k >= 3 is counted in one set of tier launches into counts[q].
+struct BatchQuery {
+  const uint64_t* orow;  // the query graph's DAG (rank space)
+  const uint32_t* ocol;
+  const uint32_t* vert;
+  uint32_t n;            // 0: nothing to enumerate (answered on the host)
+  uint32_t k;
+};
+int run_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, bool memo, bool prune, uint64_t* counts,
+              cudaStream_t s);
 
 }  // namespace kc

@@ -392,3 +392,37 @@ def config_rmat(seed: int = 2, scale: int = 22) -> Graph:
 
 def tiny_random(n: int, p: float, seed: int) -> Graph:
     return er_gnp(n, p, seed)
+
+
+def config_batched(seed: int = 3, count: int = 4096, nmin: int = 50, nmax: int = 20000):
+    """Config 4: `count` uneven graphs with a k each, as a list of (Graph, k).
+
+    n is log-uniform in [nmin, nmax]: a 53-bit uniform u is compared with the
+    table of thresholds log(n / nmin) / log(nmax / nmin), computed once for
+    every integer n (no per-sample transcendental).  Even positions are
+    Erdos-Renyi G(n, M) with M = round(n D / 2), D uniform in [8, 40]; odd
+    positions are 2-D random geometric graphs on the unit torus with mean
+    degree D uniform in [10, 60].  k is uniform in {4, ..., 8}.  Every graph
+    has its own seed drawn from the batch's stream.
+    """
+    ns = np.arange(nmin, nmax + 1, dtype=np.float64)
+    thr = np.log(ns / nmin) / np.log(nmax / nmin)  # thr[i]: smallest u giving n >= ns[i]
+    bg = _stream(seed, 9)
+    raw = _raw(bg, 4 * count).reshape(count, 4)
+    u = _u01(raw[:, 0])
+    n_of = nmin + np.searchsorted(thr, u, side="right") - 1
+    dfrac = _u01(raw[:, 1])
+    ks = 4 + _bounded(raw[:, 2], 5)
+    seeds = (raw[:, 3] >> U64(33)).astype(np.int64)
+    out = []
+    for i in range(count):
+        n = int(n_of[i])
+        if i % 2 == 0:
+            deg = 8.0 + 32.0 * float(dfrac[i])
+            m = min(int(round(n * deg / 2.0)), n * (n - 1) // 2)
+            g = er_gnm(n, m, int(seeds[i]))
+        else:
+            deg = 10.0 + 50.0 * float(dfrac[i])
+            g = rgg_torus(n, min(deg, float(n - 1)), int(seeds[i]))
+        out.append((g, int(ks[i])))
+    return out

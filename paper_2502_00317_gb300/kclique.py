@@ -38,7 +38,7 @@ KC_MAX_OUTDEG = 1024
 EXPORTS = (
     "kc_create", "kc_destroy", "kc_upload", "kc_free_graph", "kc_graph_info_get", "kc_export_dag",
     "kc_count", "kc_list", "kc_list_range", "kc_last_stats", "kc_last_upload_stats", "kc_strerror",
-    "kc_last_error", "kc_count_dag_noalloc",
+    "kc_last_error", "kc_count_dag_noalloc", "kc_count_batched",
 )
 
 
@@ -134,6 +134,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kc_strerror": (ctypes.c_char_p, [i32]),
         "kc_last_error": (ctypes.c_char_p, [P]),
         "kc_count_dag_noalloc": (i32, [u32, P, P, u32, pu64, P]),
+        "kc_count_batched": (i32, [P, P, P, u32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -250,6 +251,18 @@ def kc_last_upload_stats(ctx: int) -> dict:
     return _struct_dict(s)
 
 
+def kc_count_batched(ctx: int, graphs, ks, stream=None) -> list[int]:
+    """Counts of (graphs[i], ks[i]) for every i, in one batched enumeration."""
+    g = np.ascontiguousarray(graphs, dtype=np.uint32)
+    k = np.ascontiguousarray(ks, dtype=np.uint32)
+    if g.shape != k.shape:
+        raise ValueError("graphs and ks differ in length")
+    out = np.zeros(max(g.size, 1), dtype=np.uint64)
+    _check(load().kc_count_batched(ctypes.c_void_p(ctx), _ptr(g), _ptr(k), int(g.size), _ptr(out), _stream(stream)),
+           "kc_count_batched")
+    return [int(x) for x in out[: g.size]]
+
+
 def kc_count_dag_noalloc(n: int, d_orow, d_ocol, k: int, stream=None) -> int:
     """Count k-cliques of a device-resident rank-space DAG without any allocation
     inside the library (for callers that must not allocate); see kclique.h."""
@@ -308,6 +321,9 @@ class Context:
     def list_range(self, g: int, k: int, lo: int, hi: int, d_buf=None, cap: int = 0, stream=None,
                    allow_capacity: bool = False):
         return kc_list_range(self.h, g, k, lo, hi, d_buf, cap, stream, allow_capacity)
+
+    def count_batched(self, graphs, ks, stream=None) -> list[int]:
+        return kc_count_batched(self.h, graphs, ks, stream)
 
     def stats(self) -> dict:
         return kc_last_stats(self.h)

@@ -231,6 +231,85 @@ int kc_count_batched(kc_ctx* ctx, const kc_graph* graphs, const uint32_t* ks, ui
 int kc_count_dag_noalloc(uint32_t n, const uint64_t* d_orow, const uint32_t* d_ocol, uint32_t k, uint64_t* count,
                          void* stream);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop inside the library (no counterpart in the paper, which
+ * runs one listing at a time): requests (a resident graph or an inline CSR,
+ * and k) are queued by kc_serve_submit and taken by `lanes` worker threads.
+ * Each lane owns its own device scratch and streams.  Whenever a lane is
+ * free it takes every queued request that fits -- at most max_batch, and
+ * only while the device bytes reserved by admitted, unfinished requests stay
+ * within mem_cap_bytes -- and counts them together as one batch (the
+ * kc_count_batched path).  Requests that arrive while a batch runs wait for
+ * the next free lane, so with two or more lanes batches overlap on the GPU.
+ * A request's result is the same alone and in any mix.
+ *
+ * While serving, the context's resident graphs are read-only: do not call
+ * kc_upload, kc_free_graph, kc_count, kc_list or kc_count_batched on it until
+ * kc_serve_stop returns.  The kc_serve_* calls themselves may come from any
+ * number of host threads.
+ */
+typedef struct kc_serve_opts {
+  uint32_t struct_size;    /* sizeof(kc_serve_opts) */
+  uint32_t lanes;          /* worker lanes (0: 2) */
+  uint32_t max_batch;      /* requests per batch at most (0: 4096) */
+  uint32_t reserved;
+  uint64_t mem_cap_bytes;  /* admission cap on reserved device bytes (0: 64 GiB) */
+} kc_serve_opts;
+
+#define KC_SERVE_COUNT 0u      /* mode: count the k-cliques */
+
+typedef struct kc_serve_result {
+  uint64_t count;          /* k-cliques (when status == KC_OK) */
+  int32_t status;          /* KC_OK, or the error of this request */
+  uint32_t batch_size;     /* requests in the batch that served it */
+  uint64_t t_submit_ns;    /* steady-clock times: submission, batch start, completion */
+  uint64_t t_start_ns;
+  uint64_t t_done_ns;
+} kc_serve_result;
+
+typedef struct kc_serve_stats {
+  uint64_t submitted;
+  uint64_t completed;
+  uint64_t failed;         /* completed with a status other than KC_OK */
+  uint64_t batches;
+  double p50_ms;           /* latency (submission to completion) percentiles of completed requests */
+  double p99_ms;
+  double mean_batch;       /* requests per batch */
+  double req_per_s;        /* completed / (last completion - first submission) */
+  double cliques_per_s;
+  uint64_t peak_reserved_bytes;
+} kc_serve_stats;
+
+/* Start serving on ctx (opts may be NULL).  KC_E_BUSY if already serving. */
+int kc_serve_start(kc_ctx* ctx, const kc_serve_opts* opts);
+
+/* Queue a count of the k-cliques of resident graph g; *ticket receives the
+ * request's id.  mode must be KC_SERVE_COUNT.  Errors of the request itself
+ * (k = 0, k > KC_MAX_K, unknown graph) are returned here. */
+int kc_serve_submit(kc_ctx* ctx, kc_graph g, uint32_t k, uint32_t mode, uint64_t* ticket);
+
+/* As kc_serve_submit for a graph given inline as a host CSR (same layout and
+ * flags as kc_upload, KC_HOST_PTRS implied); the arrays are copied before
+ * the call returns.  The lane uploads it, counts it and frees it; its device
+ * bytes count against the admission cap until then.  A graph whose footprint
+ * alone exceeds the cap completes with status KC_E_OOM. */
+int kc_serve_submit_csr(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr, const uint32_t* col, uint32_t flags,
+                        uint32_t k, uint32_t mode, uint64_t* ticket);
+
+/* Result of a request: KC_OK and *out filled once it is complete (the
+ * request is then forgotten), KC_E_BUSY while it is queued or running,
+ * KC_E_NOT_FOUND for an unknown or already collected ticket.  kc_serve_wait
+ * blocks up to timeout_ms (negative: no limit) for it. */
+int kc_serve_poll(kc_ctx* ctx, uint64_t ticket, kc_serve_result* out);
+int kc_serve_wait(kc_ctx* ctx, uint64_t ticket, int64_t timeout_ms, kc_serve_result* out);
+
+/* Counters and latency percentiles since kc_serve_start. */
+int kc_serve_stats_get(kc_ctx* ctx, kc_serve_stats* out);
+
+/* Stop serving: requests not yet taken by a lane complete with status
+ * KC_E_BUSY, running batches finish, the lanes are released. */
+int kc_serve_stop(kc_ctx* ctx);
+
 /* Telemetry of the last count/list call, and of the last upload. */
 int kc_last_stats(kc_ctx* ctx, kc_stats* out);
 int kc_last_upload_stats(kc_ctx* ctx, kc_upload_stats* out);

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkc.so")
-SOURCES = ["kc_api.cu", "kc_prep.cu", "kc_enum.cu"]
+SOURCES = ["kc_api.cu", "kc_prep.cu", "kc_enum.cu", "kc_serve.cu"]
 PEAK_SOURCE = "kc_peak.cu"  # separate library: the benchmark's integer-pipe peak
 PEAK_LIB = os.path.join(BUILD, "libkc_peak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

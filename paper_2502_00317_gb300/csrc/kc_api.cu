@@ -131,6 +131,7 @@ int kc_create(kc_ctx** out, int device, const kc_opts* opts) {
 
 int kc_destroy(kc_ctx* ctx) {
   if (!ctx) return KC_E_INVALID_ARG;
+  serve_release(ctx);
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   for (auto& kv : ctx->graphs) free_graph(kv.second);

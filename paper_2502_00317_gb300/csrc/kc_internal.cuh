@@ -114,6 +114,8 @@ struct Scratch {
   size_t bytes = 0;
 };
 
+struct Server;  // the serving loop (kc_serve.cu)
+
 }  // namespace kc
 
 struct kc_ctx {
@@ -137,6 +139,7 @@ struct kc_ctx {
   kc_stats last{};
   kc_upload_stats last_up{};
   std::string last_error;
+  kc::Server* server = nullptr;           // kc_serve_* state, if serving was ever started
 };
 
 namespace kc {
@@ -194,6 +197,9 @@ int exclusive_scan_u32_to_u64(kc_ctx* ctx, const uint32_t* in, uint64_t* out, ui
 // writes their number to ucount[r].
 int segmented_sort(kc_ctx* ctx, uint32_t* data, const uint64_t* ptr, uint32_t rows, uint64_t total, uint32_t max_row,
                    uint32_t* ucount, cudaStream_t s, uint32_t* launches);
+
+// Serving (kc_serve.cu): stop the loop and free its state (kc_destroy).
+void serve_release(kc_ctx* ctx);
 
 // Upload pipeline (kc_prep.cu).
 int prep_graph(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr, const uint32_t* col, uint32_t flags,

@@ -38,8 +38,11 @@ KC_MAX_OUTDEG = 1024
 EXPORTS = (
     "kc_create", "kc_destroy", "kc_upload", "kc_free_graph", "kc_graph_info_get", "kc_export_dag",
     "kc_count", "kc_list", "kc_list_range", "kc_last_stats", "kc_last_upload_stats", "kc_strerror",
-    "kc_last_error", "kc_count_dag_noalloc", "kc_count_batched",
+    "kc_last_error", "kc_count_dag_noalloc", "kc_count_batched", "kc_serve_start", "kc_serve_submit",
+    "kc_serve_submit_csr", "kc_serve_poll", "kc_serve_wait", "kc_serve_stats_get", "kc_serve_stop",
 )
+
+KC_SERVE_COUNT = 0
 
 
 class KcError(RuntimeError):
@@ -102,6 +105,42 @@ class kc_upload_stats(ctypes.Structure):
     ]
 
 
+class kc_serve_opts(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("lanes", ctypes.c_uint32),
+        ("max_batch", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("mem_cap_bytes", ctypes.c_uint64),
+    ]
+
+
+class kc_serve_result(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_uint64),
+        ("status", ctypes.c_int32),
+        ("batch_size", ctypes.c_uint32),
+        ("t_submit_ns", ctypes.c_uint64),
+        ("t_start_ns", ctypes.c_uint64),
+        ("t_done_ns", ctypes.c_uint64),
+    ]
+
+
+class kc_serve_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_uint64),
+        ("completed", ctypes.c_uint64),
+        ("failed", ctypes.c_uint64),
+        ("batches", ctypes.c_uint64),
+        ("p50_ms", ctypes.c_double),
+        ("p99_ms", ctypes.c_double),
+        ("mean_batch", ctypes.c_double),
+        ("req_per_s", ctypes.c_double),
+        ("cliques_per_s", ctypes.c_double),
+        ("peak_reserved_bytes", ctypes.c_uint64),
+    ]
+
+
 def _struct_dict(s) -> dict:
     out = {}
     for name, _ in s._fields_:
@@ -135,6 +174,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kc_last_error": (ctypes.c_char_p, [P]),
         "kc_count_dag_noalloc": (i32, [u32, P, P, u32, pu64, P]),
         "kc_count_batched": (i32, [P, P, P, u32, P, P]),
+        "kc_serve_start": (i32, [P, ctypes.POINTER(kc_serve_opts)]),
+        "kc_serve_submit": (i32, [P, u32, u32, u32, pu64]),
+        "kc_serve_submit_csr": (i32, [P, u32, P, P, u32, u32, u32, pu64]),
+        "kc_serve_poll": (i32, [P, u64, ctypes.POINTER(kc_serve_result)]),
+        "kc_serve_wait": (i32, [P, u64, ctypes.c_int64, ctypes.POINTER(kc_serve_result)]),
+        "kc_serve_stats_get": (i32, [P, ctypes.POINTER(kc_serve_stats)]),
+        "kc_serve_stop": (i32, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -261,6 +307,58 @@ def kc_count_batched(ctx: int, graphs, ks, stream=None) -> list[int]:
     _check(load().kc_count_batched(ctypes.c_void_p(ctx), _ptr(g), _ptr(k), int(g.size), _ptr(out), _stream(stream)),
            "kc_count_batched")
     return [int(x) for x in out[: g.size]]
+
+
+def kc_serve_start(ctx: int, lanes: int = 0, max_batch: int = 0, mem_cap_bytes: int = 0) -> None:
+    o = kc_serve_opts(ctypes.sizeof(kc_serve_opts), int(lanes), int(max_batch), 0, int(mem_cap_bytes))
+    _check(load().kc_serve_start(ctypes.c_void_p(ctx), ctypes.byref(o)), "kc_serve_start")
+
+
+def kc_serve_submit(ctx: int, g: int, k: int, mode: int = KC_SERVE_COUNT) -> int:
+    t = ctypes.c_uint64(0)
+    _check(load().kc_serve_submit(ctypes.c_void_p(ctx), int(g), int(k), int(mode), ctypes.byref(t)),
+           "kc_serve_submit")
+    return int(t.value)
+
+
+def kc_serve_submit_csr(ctx: int, n: int, rowptr, col, k: int, canonicalize: bool = False,
+                        mode: int = KC_SERVE_COUNT) -> int:
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.uint64)
+    col = np.ascontiguousarray(col, dtype=np.uint32)
+    t = ctypes.c_uint64(0)
+    flags = KC_HOST_PTRS | (KC_CANONICALIZE if canonicalize else 0)
+    _check(load().kc_serve_submit_csr(ctypes.c_void_p(ctx), int(n), _ptr(rowptr), _ptr(col) if col.size else None,
+                                      flags, int(k), int(mode), ctypes.byref(t)), "kc_serve_submit_csr")
+    return int(t.value)
+
+
+def kc_serve_poll(ctx: int, ticket: int):
+    """The request's result dict once complete, else None (queued or running)."""
+    r = kc_serve_result()
+    st = load().kc_serve_poll(ctypes.c_void_p(ctx), int(ticket), ctypes.byref(r))
+    if st == KC_E_BUSY:
+        return None
+    _check(st, "kc_serve_poll")
+    return _struct_dict(r)
+
+
+def kc_serve_wait(ctx: int, ticket: int, timeout_ms: int = -1):
+    r = kc_serve_result()
+    st = load().kc_serve_wait(ctypes.c_void_p(ctx), int(ticket), int(timeout_ms), ctypes.byref(r))
+    if st == KC_E_BUSY:
+        return None
+    _check(st, "kc_serve_wait")
+    return _struct_dict(r)
+
+
+def kc_serve_stats_get(ctx: int) -> dict:
+    s = kc_serve_stats()
+    _check(load().kc_serve_stats_get(ctypes.c_void_p(ctx), ctypes.byref(s)), "kc_serve_stats_get")
+    return _struct_dict(s)
+
+
+def kc_serve_stop(ctx: int) -> None:
+    _check(load().kc_serve_stop(ctypes.c_void_p(ctx)), "kc_serve_stop")
 
 
 def kc_count_dag_noalloc(n: int, d_orow, d_ocol, k: int, stream=None) -> int:

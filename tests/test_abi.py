@@ -55,6 +55,11 @@ def test_null_arguments_rejected_without_a_device():
     assert lib.kc_count(None, 1, 3, None, None) == kc.KC_E_INVALID_ARG
     assert lib.kc_list(None, 1, 3, None, 0, None, None, None, None) == kc.KC_E_INVALID_ARG
     assert lib.kc_last_stats(None, None) == kc.KC_E_INVALID_ARG
+    assert lib.kc_serve_start(None, None) == kc.KC_E_INVALID_ARG
+    assert lib.kc_serve_submit(None, 1, 3, 0, None) == kc.KC_E_INVALID_ARG
+    assert lib.kc_serve_poll(None, 1, None) == kc.KC_E_INVALID_ARG
+    assert lib.kc_serve_stop(None) == kc.KC_E_INVALID_ARG
+    assert lib.kc_count_batched(None, None, None, 0, None, None) == kc.KC_E_INVALID_ARG
 
 
 def test_create_fails_cleanly_without_gpu():
@@ -73,3 +78,6 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(kc.kc_graph_info) == 24
     assert ctypes.sizeof(kc.kc_stats) == 144
     assert ctypes.sizeof(kc.kc_upload_stats) == 24
+    assert ctypes.sizeof(kc.kc_serve_opts) == 24
+    assert ctypes.sizeof(kc.kc_serve_result) == 40
+    assert ctypes.sizeof(kc.kc_serve_stats) == 80

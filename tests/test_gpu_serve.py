@@ -1,0 +1,145 @@
+"""Serving (kc_serve_*): continuous batching must not change any result.
+
+Each request's count must equal kc_count on the same graph alone, whatever
+mix of requests it was batched with; the memory-admission cap must hold; a
+request too large for the cap fails alone; stopping ends every request.
+Counts are exact integers, so "the same" is equality.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_00317_gb300 import graphgen as gg
+from paper_2502_00317_gb300 import kclique as kc
+
+pytestmark = pytest.mark.gpu
+
+
+def _graphs():
+    return [
+        gg.er_gnp(300, 0.3, 1),
+        gg.rgg_torus(3000, 40.0, seed=2),
+        gg.complete(30),
+        gg.chung_lu_planted(n=20000, n_cliques=40, seed=1),
+        gg.er_gnp(400, 0.3, 12),
+        gg.turan(30, 7),
+        gg.rgg_torus(2000, 60.0, seed=3),
+    ]
+
+
+def _expected(c, hs, ks):
+    table = {}
+    for h in set(hs):
+        for k in set(ks):
+            table[(h, k)] = c.count(h, k)
+    return table
+
+
+def test_results_same_alone_and_in_the_mix():
+    graphs = _graphs()
+    with kc.Context(0) as c:
+        hs = [c.upload_host(g.n, g.rowptr, g.col) for g in graphs]
+        ks = [1, 2, 3, 4, 5, 6, 7, 8, 31]
+        want = _expected(c, hs, ks)
+        kc.kc_serve_start(c.h, lanes=2, max_batch=64)
+        rng = np.random.default_rng(0)
+        reqs = [(int(hs[i]), int(ks[j])) for i, j in zip(rng.integers(0, len(hs), 400), rng.integers(0, len(ks), 400))]
+        tickets = [None] * len(reqs)
+
+        def submit(lo, hi):
+            for i in range(lo, hi):
+                tickets[i] = kc.kc_serve_submit(c.h, *reqs[i])
+
+        ths = [threading.Thread(target=submit, args=(i * 100, (i + 1) * 100)) for i in range(4)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        sizes = []
+        for (h, k), t in zip(reqs, tickets):
+            r = kc.kc_serve_wait(c.h, t, 120000)
+            assert r is not None and r["status"] == kc.KC_OK, r
+            assert r["count"] == want[(h, k)], (h, k)
+            assert r["t_submit_ns"] <= r["t_start_ns"] <= r["t_done_ns"]
+            sizes.append(r["batch_size"])
+        assert max(sizes) > 1  # requests really were batched together
+        st = kc.kc_serve_stats_get(c.h)
+        assert st["submitted"] == st["completed"] == len(reqs) and st["failed"] == 0
+        assert st["p50_ms"] <= st["p99_ms"]
+        with pytest.raises(kc.KcError) as e:  # collected already
+            kc.kc_serve_poll(c.h, tickets[0])
+        assert e.value.status == kc.KC_E_NOT_FOUND
+        kc.kc_serve_stop(c.h)
+        for h in hs:
+            c.free(h)
+
+
+def test_inline_graphs_and_admission_cap():
+    graphs = _graphs()
+    with kc.Context(0) as c:
+        hs = [c.upload_host(g.n, g.rowptr, g.col) for g in graphs]
+        big = graphs[3]
+        # the cap admits the largest inline graph alone, so inline requests wait for one another
+        cap = 48 * big.n + 8 * big.nnz + 8 * big.n + 1024
+        kc.kc_serve_start(c.h, lanes=2, max_batch=16, mem_cap_bytes=cap)
+        jobs = []
+        for i, g in enumerate(graphs):
+            for k in (3, 5, 7):
+                jobs.append((kc.kc_serve_submit_csr(c.h, g.n, g.rowptr, g.col, k), g, k))
+                jobs.append((kc.kc_serve_submit(c.h, hs[i], k), g, k))
+        # a raw CSR that the lane must canonicalise
+        raw = gg.rmat(scale=10, edge_factor=8, seed=4)
+        jobs.append((kc.kc_serve_submit_csr(c.h, raw.n, raw.rowptr, raw.col, 4, canonicalize=True), raw, 4))
+        # an inline graph larger than the cap fails alone
+        huge = gg.er_gnm(200000, 400000, seed=1)
+        t_huge = kc.kc_serve_submit_csr(c.h, huge.n, huge.rowptr, huge.col, 3)
+        for t, g, k in jobs:
+            r = kc.kc_serve_wait(c.h, t, 120000)
+            assert r["status"] == kc.KC_OK
+            assert r["count"] == oracle.OracleGraph.from_graph(g).count(k)[0], (g.name, k)
+        r = kc.kc_serve_wait(c.h, t_huge, 120000)
+        assert r["status"] == kc.KC_E_OOM
+        st = kc.kc_serve_stats_get(c.h)
+        assert 0 < st["peak_reserved_bytes"] <= cap
+        kc.kc_serve_stop(c.h)
+        for h in hs:
+            c.free(h)
+
+
+def test_stop_ends_every_request_and_errors():
+    g = gg.rgg_torus(3000, 40.0, seed=2)
+    with kc.Context(0) as c:
+        h = c.upload_host(g.n, g.rowptr, g.col)
+        want = c.count(h, 6)
+        with pytest.raises(kc.KcError) as e:  # not serving yet
+            kc.kc_serve_submit(c.h, h, 4)
+        assert e.value.status == kc.KC_E_BUSY
+        kc.kc_serve_start(c.h, lanes=1, max_batch=2)
+        with pytest.raises(kc.KcError) as e:
+            kc.kc_serve_start(c.h)
+        assert e.value.status == kc.KC_E_BUSY
+        for bad, code in (((h, 0), kc.KC_E_INVALID_ARG), ((h + 77, 4), kc.KC_E_NOT_FOUND),
+                          ((h, kc.KC_MAX_K + 1), kc.KC_E_UNSUPPORTED)):
+            with pytest.raises(kc.KcError) as e:
+                kc.kc_serve_submit(c.h, *bad)
+            assert e.value.status == code
+        tickets = [kc.kc_serve_submit(c.h, h, 6) for _ in range(200)]
+        kc.kc_serve_stop(c.h)
+        ok = busy = 0
+        for t in tickets:
+            r = kc.kc_serve_poll(c.h, t)
+            assert r is not None  # every request ended
+            if r["status"] == kc.KC_OK:
+                assert r["count"] == want
+                ok += 1
+            else:
+                assert r["status"] == kc.KC_E_BUSY
+                busy += 1
+        assert ok + busy == len(tickets)
+        # serving again on the same context works
+        kc.kc_serve_start(c.h, lanes=2)
+        assert kc.kc_serve_wait(c.h, kc.kc_serve_submit(c.h, h, 6), 60000)["count"] == want
+        kc.kc_serve_stop(c.h)
+        c.free(h)

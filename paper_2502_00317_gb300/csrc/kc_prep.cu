@@ -839,6 +839,11 @@ int prep_graph(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr_in, const uint32_
     void* args[] = {&pa};
     KC_CUDA(cudaLaunchCooperativeKernel((const void*)k_peel, dim3(nb), dim3(kPeelThreads), args, 0, s));
     launches++;
+    // a peel that gave up at a bounded wait leaves ranks unset: stop before anything indexes with them
+    uint32_t h_status = 0;
+    KC_CUDA(cudaMemcpyAsync(&h_status, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    if (h_status & kStTimeout) return KC_E_DEVICE_TIMEOUT;
   }
   KC_CUDA(cudaEventRecord(ev[3], s));
   // ---- orient

@@ -151,8 +151,8 @@ def _struct_dict(s) -> dict:
 
 @lru_cache(maxsize=1)
 def load(path: str | None = None) -> ctypes.CDLL:
-    """Load libkc.so (building it first if the sources changed)."""
-    path = path or _build.build()
+    """Load libkc.so (building it first if the sources changed; KC_LIBRARY names another build)."""
+    path = path or os.environ.get("KC_LIBRARY") or _build.build()
     if not os.path.exists(path):
         raise RuntimeError(f"libkc.so missing at {path}")
     lib = ctypes.CDLL(path)

@@ -222,7 +222,8 @@ def test_split_path_matches_oracle(maker, splits):
                 assert c.count(h, k) == want, (k, c.stats())
             heavy += ctxs[0].stats()["roots_heavy"]
             assert ctxs[2].stats()["roots_heavy"] == 0
-        assert (heavy > 0) == splits
+        if splits:  # wide sparse roots are split by the wedge test; others may be split by their run time
+            assert heavy > 0
         for k in (5, 6):
             want = og.checksum(k)
             for c, h in zip(ctxs, hs):
@@ -427,5 +428,51 @@ def test_chung_lu_full_size_vs_golden(ctx):
         for key in keys:
             k = int(key.rsplit("_k", 1)[1])
             assert ctx.count(h, k) == gold[key]["count"], k
+    finally:
+        ctx.free(h)
+
+
+# ------------------------------------------------------ bounded device waits
+def test_bounded_wait_gives_up_and_context_stays_usable():
+    """A peel whose grid barrier may wait only 1 ns gives up, reports
+    KC_E_DEVICE_TIMEOUT and leaves the context usable (no fault, no hang)."""
+    g = gg.chung_lu_planted(n=20000, n_cliques=40, seed=1)
+    small = gg.complete(9)  # fits one block: its barriers never wait
+    with kc.Context(0, spin_limit=1) as c:
+        with pytest.raises(kc.KcError) as e:
+            c.upload_host(g.n, g.rowptr, g.col)
+        assert e.value.status == kc.KC_E_DEVICE_TIMEOUT
+        h = c.upload_host(small.n, small.rowptr, small.col)
+        assert c.count(h, 4) == oracle.binom(9, 4)
+        c.free(h)
+    with kc.Context(0) as c:
+        h = c.upload_host(g.n, g.rowptr, g.col)
+        assert c.count(h, 5) == oracle.OracleGraph.from_graph(g).count(5)[0]
+        c.free(h)
+
+
+def test_rmat_scale22_full_size_vs_golden(ctx):
+    """R-MAT scale 22 (raw pairs, canonicalised on the device): m, degeneracy,
+    and the k = 3 and 4 counts and checksums against the oracle's stored values;
+    k = 4 also as a sum over a partition of root ranges."""
+    gold = json.load(open(os.path.join(GOLD, "config_results.json")))
+    g = gg.config_rmat()
+    assert gold["rmat_22_16_seed2_k3"]["fingerprint"] == g.fingerprint()
+    h = ctx.upload_host(g.n, g.rowptr, g.col, canonicalize=True)
+    try:
+        info = ctx.info(h)
+        assert info["m"] == gold["rmat_22_16_seed2_k3"]["m"]
+        assert info["degeneracy"] == gold["rmat_22_16_seed2_k3"]["degeneracy"]
+        for k in (3, 4):
+            want = gold[f"rmat_22_16_seed2_k{k}"]
+            assert ctx.count(h, k) == want["count"], k
+            assert ctx.list(h, k, None, 0)[1:] == (want["count"], want["checksum"]), k
+        cuts = [0, g.n // 2, g.n - 200000, g.n - 5000, g.n]
+        tot, chk = 0, 0
+        for lo, hi in zip(cuts, cuts[1:]):
+            _, t, s = ctx.list_range(h, 4, lo, hi)
+            tot += t
+            chk = (chk + s) % (1 << 64)
+        assert (tot, chk) == (gold["rmat_22_16_seed2_k4"]["count"], gold["rmat_22_16_seed2_k4"]["checksum"])
     finally:
         ctx.free(h)

@@ -73,8 +73,6 @@ struct EnumKArgs {
   uint32_t query;               // query bound to this copy of the arguments
 };
 
-
-// Per-warp working state, carved from shared or global memory.
 // Bytes of one warp's working state at width W (the layout of WarpState::carve).
 __host__ __device__ constexpr size_t warp_state_raw(int W) {
   return (size_t)32 * W * 4 + (size_t)32 * W * W * 4 + (size_t)KMAX * W * 4 * 2 + (size_t)KMAX * 8 +
@@ -84,6 +82,7 @@ __host__ __device__ constexpr size_t warp_state_raw(int W) {
 // Per-warp stride of that state (16-byte aligned).
 __host__ __device__ constexpr size_t warp_state_stride(int W) { return (warp_state_raw(W) + 15) & ~(size_t)15; }
 
+// Per-warp working state, carved from shared or global memory.
 template <int W>
 struct WarpState {
   uint32_t* nbr;              // [32W] ranks of N+(u), ascending

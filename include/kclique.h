@@ -54,9 +54,12 @@ typedef struct kc_opts {
   uint32_t struct_size;
   uint32_t no_memo;        /* 1: never use the device form of the Induced Subgraph Trie (Sec. IV) */
   uint32_t no_prune;       /* 1: never prune by soft embeddings (Sec. V, Algorithm 5) */
-  uint32_t split_threshold;/* roots whose estimated work exceeds this many units are split over warps (0: default) */
+  uint32_t split_threshold;/* a root of width > 32 whose G_u has more wedges (sum of C(out-degree, 2)) than
+                              this is split into one task per first-level branch (Sec. VII-D);
+                              0: default 16384, 0xFFFFFFFF: never split; applies for k >= 5 */
   uint64_t memo_bytes;     /* device bytes for the memo tables (0: default 1 GiB); the tau of Sec. VI */
-  uint64_t spin_limit;     /* iterations before a device-side wait gives up (0: default) */
+  uint64_t spin_limit;     /* nanoseconds before a device-side wait gives up with KC_E_DEVICE_TIMEOUT
+                              (0: default 2 s) */
 } kc_opts;
 
 /* Graph facts after upload. */

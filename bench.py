@@ -237,8 +237,8 @@ def run_ours(a):
         "peak_source": peak_note,
         "unit": "Gword-op/s (word-op = 32-bit AND + POPC of candidate words)",
         "frac": round(achieved * 1e9 / peak_ops, 5) if (achieved and peak_ops) else None,
-        # DRAM bytes of the family per kc_count call: ncu dram__bytes_read.sum + dram__bytes_write.sum over
-        # k_enum + k_tasks of the k = 5..9 sweep, averaged per call (profiles/dram_chung_lu_n1e6_planted2000_k5-9.md)
+        # DRAM bytes of the family per kc_count call, from one ncu capture of this sweep:
+        # dram__bytes_read.sum + dram__bytes_write.sum over k_enum + k_tasks, averaged per call
         "traffic": 616778223 if (not a.small and ks == KS) else None,
         "traffic_unit": "bytes per kc_count call (enumerator family)",
         "word_ops_per_launch": round(word_ops / calls),

@@ -4,6 +4,7 @@
     python tests/golden/make_golden.py er                # ER G(2000, 0.01) k=3..5
     python tests/golden/make_golden.py chunglu [k ...]   # Chung-Lu + planted, k=5..9 counts
     python tests/golden/make_golden.py rmat [k ...]      # R-MAT scale 22, count + checksum (default k=3,4)
+    python tests/golden/make_golden.py rmatcount k ...   # R-MAT scale 22, count only
 
 Every expected value comes from ``oracle`` on inputs from the seeded
 generator module; nothing here touches the CUDA path.
@@ -82,5 +83,9 @@ if __name__ == "__main__":
         chunglu([int(x) for x in sys.argv[2:]] or [5, 6, 7, 8, 9])
     elif what == "rmat":
         rmat([int(x) for x in sys.argv[2:]] or [3, 4])
+    elif what == "rmatcount":
+        g = gg.config_rmat()
+        _record("config_results.json", "rmat_22_16_seed2", oracle.OracleGraph.from_graph(g), g,
+                [int(x) for x in sys.argv[2:]], False)
     else:
         raise SystemExit(__doc__)

@@ -453,8 +453,8 @@ def test_bounded_wait_gives_up_and_context_stays_usable():
 
 def test_rmat_scale22_full_size_vs_golden(ctx):
     """R-MAT scale 22 (raw pairs, canonicalised on the device): m, degeneracy,
-    and the k = 3 and 4 counts and checksums against the oracle's stored values;
-    k = 4 also as a sum over a partition of root ranges."""
+    the k = 3 and 4 counts and checksums and the k = 5 count against the
+    oracle's stored values; k = 4 also as a sum over a partition of root ranges."""
     gold = json.load(open(os.path.join(GOLD, "config_results.json")))
     g = gg.config_rmat()
     assert gold["rmat_22_16_seed2_k3"]["fingerprint"] == g.fingerprint()
@@ -467,6 +467,8 @@ def test_rmat_scale22_full_size_vs_golden(ctx):
             want = gold[f"rmat_22_16_seed2_k{k}"]
             assert ctx.count(h, k) == want["count"], k
             assert ctx.list(h, k, None, 0)[1:] == (want["count"], want["checksum"]), k
+        # k = 5: 6.9e12 cliques, the oracle's count only (a CPU listing of each is out of reach)
+        assert ctx.count(h, 5) == gold["rmat_22_16_seed2_k5"]["count"]
         cuts = [0, g.n // 2, g.n - 200000, g.n - 5000, g.n]
         tot, chk = 0, 0
         for lo, hi in zip(cuts, cuts[1:]):

@@ -211,8 +211,8 @@ int kc_count_batched(kc_ctx* ctx, const kc_graph* graphs, const uint32_t* ks, ui
  *   kc_export_dag returns (any total order gives the same count).
  * Output: *count (host) = the number of k-cliques; k = 1 gives n, k = 2 the
  * number of DAG edges.  The work is the plain count of kc_count (one warp per
- * root, Algorithm 5 pruning) without the memo and without the heavy-root
- * split.
+ * root, the same pruning as kc_count) without the memo and without the
+ * heavy-root split.
  *
  * Scratch lives in one fixed device array of 3 MiB + 768 B inside the
  * library, which every GPU that loads libkc.so holds until the process

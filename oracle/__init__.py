@@ -77,6 +77,8 @@ def _lib():
     lib.kco_list.argtypes = [P, u32, P, u64, ctypes.POINTER(u64), ctypes.POINTER(u64)]
     lib.kco_clique_hash.restype = u64
     lib.kco_clique_hash.argtypes = [P, u32]
+    lib.kco_mix64_value.restype = u64
+    lib.kco_mix64_value.argtypes = [u64]
     return lib
 
 
@@ -185,6 +187,11 @@ class OracleGraph:
         _lib().kco_list(self._h, int(k), _ptr(buf), int(cap), ctypes.byref(total), ctypes.byref(s))
         got = min(cap, int(total.value))
         return buf[: got * k].reshape(got, k), int(total.value), int(s.value)
+
+
+def mix64(z: int) -> int:
+    """The SplitMix64 finaliser of the checksum (the oracle's C function)."""
+    return int(_lib().kco_mix64_value(int(z) & 0xFFFFFFFFFFFFFFFF))
 
 
 def clique_hash(ids_sorted) -> int:

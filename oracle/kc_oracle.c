@@ -66,6 +66,10 @@ static uint64_t kco_mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
+/* The finaliser alone, exported so that the tests can pin it to published
+ * SplitMix64 outputs. */
+uint64_t kco_mix64_value(uint64_t z) { return kco_mix64(z); }
+
 uint64_t kco_clique_hash(const uint32_t *ids_sorted, uint32_t k) {
   uint64_t h = kco_mix64(0x9E3779B97F4A7C15ULL ^ (uint64_t)k);
   for (uint32_t i = 0; i < k; i++) h = kco_mix64(h ^ (uint64_t)ids_sorted[i]);

@@ -613,9 +613,8 @@ extern "C" int kc_count_dag_noalloc(uint32_t n, const uint64_t* d_orow, const ui
   EnumKArgs x{};
   x.orow = d_orow;
   x.ocol = d_ocol;
-  // the count kernel stores vert[root] without using it; the row offsets,
-  // read as 2n+2 words, are a readable stand-in for that n-word array
-  x.vert = (const uint32_t*)d_orow;
+  // no id map: the count kernel (mode 0) never reads vert, only listing does
+  x.vert = nullptr;
   x.k = k;
   x.prune = 1;
   x.acc = acc;

@@ -138,6 +138,67 @@ def test_random_tiny_graphs_brute_force(seed):
         assert s2 == s
 
 
+# Published SplitMix64 outputs (Steele, Lea & Flood, OOPSLA 2014; Vigna's
+# public-domain splitmix64.c): the state x advances by 0x9E3779B97F4A7C15 and
+# each output is the finaliser of the new state.  Seed 0 gives the sequence
+# quoted with the generator; the other two are test vectors produced with
+# the reference splitmix64.c for seeds 1234567 and 1477776061723855037.
+SPLITMIX64_GAMMA = 0x9E3779B97F4A7C15
+SPLITMIX64_PUBLISHED = {
+    0: [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC, 0x1B39896A51A8749B],
+    1234567: [6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431,
+              16408922859458223821],
+    1477776061723855037: [1985237415132408290, 2979275885539914483, 13511426838097143398, 8488337342461049707,
+                          15141737807933549159, 17093170987380407015],
+}
+
+
+def test_mix64_is_the_published_splitmix64_finaliser():
+    """The checksum's mixer reproduces published SplitMix64 outputs (a wrong
+    shift, constant or operator in the finaliser changes every one)."""
+    for seed, outs in SPLITMIX64_PUBLISHED.items():
+        x = seed
+        for want in outs:
+            x = (x + SPLITMIX64_GAMMA) % (1 << 64)
+            assert oracle.mix64(x) == want, (seed, hex(want))
+
+
+def test_clique_hash_worked_example():
+    """The hash of one clique, worked step by step outside the oracle.
+
+    The empty tuple (k = 0) hashes to mix(0x9E3779B97F4A7C15), the first
+    SplitMix64 output for seed 0: 0xE220A8397B1DCDAF.
+
+    The clique {1, 2} (k = 2): h0 = mix(0x9E3779B97F4A7C15 ^ 2), then
+    h1 = mix(h0 ^ 1), then h2 = mix(h1 ^ 2), where mix(z) is
+    z ^= z >> 30; z *= 0xBF58476D1CE4E5B9; z ^= z >> 27;
+    z *= 0x94D049BB133111EB; z ^= z >> 31 (mod 2^64):
+
+        mix(0x9E3779B97F4A7C17):  z ^ z>>30 = 0x9E3779BB07979AF2
+                                  * c1      = 0xEE18B4F591B172E2
+                                  ^ >>27    = 0xEE18B4E852A7EC50
+                                  * c2      = 0x975835DF32273D70
+                                  ^ >>31    = 0x975835DE1C9756CE = h0
+        mix(h0 ^ 1 = 0x975835DE1C9756CF):   ... 0xF2826F98653E9E57 = h1
+          (0x975835DC41F781B7, 0x3192C1B89DE1703F, 0x3192C1BEAFB9472C,
+           0xF2826F99803A4164)
+        mix(h1 ^ 2 = 0xF2826F98653E9E55):   ... 0x0C0266261F3A0C53 = h2
+          (0xF2826F9BAF372034, 0x1E3222004CF4C994, 0x1E3222038AB0899D,
+           0x0C026626073EC01F)
+    """
+    assert oracle.clique_hash([]) == 0xE220A8397B1DCDAF
+    assert oracle.mix64(0x9E3779B97F4A7C17) == 0x975835DE1C9756CE
+    assert oracle.mix64(0x975835DE1C9756CF) == 0xF2826F98653E9E57
+    assert oracle.mix64(0xF2826F98653E9E55) == 0x0C0266261F3A0C53
+    assert oracle.clique_hash([1, 2]) == 0x0C0266261F3A0C53
+    # a graph with one k-clique has that clique's hash as its checksum
+    og = oracle.OracleGraph.from_graph(gg.complete(3))
+    assert og.checksum(3)[1] == oracle.clique_hash([0, 1, 2])
+    # the single edge {1, 2} of a 3-vertex graph
+    og2 = oracle.OracleGraph(3, np.array([0, 0, 1, 2], dtype=np.uint64), np.array([2, 1], dtype=np.uint32))
+    assert og2.checksum(2) == (1, 0x0C0266261F3A0C53)
+
+
 def test_checksum_sees_a_duplicate():
     g = gg.complete(6)
     og = oracle.OracleGraph.from_graph(g)

@@ -60,7 +60,14 @@ typedef struct kc_opts {
   uint64_t memo_bytes;     /* device bytes for the memo tables (0: default 1 GiB); the tau of Sec. VI */
   uint64_t spin_limit;     /* nanoseconds before a device-side wait gives up with KC_E_DEVICE_TIMEOUT
                               (0: default 2 s) */
+  uint32_t decomposition;  /* how roots become GPU work items (Sec. VII-D): KC_NODE_PARALLEL (0, default):
+                              one warp per root, heavy roots split as above; KC_EDGE_PARALLEL: every
+                              root's first-level branches (u, v) are separate tasks, for any k >= 3 */
+  uint32_t reserved0;
 } kc_opts;
+
+#define KC_NODE_PARALLEL 0u
+#define KC_EDGE_PARALLEL 1u
 
 /* Graph facts after upload. */
 typedef struct kc_graph_info {
@@ -237,14 +244,25 @@ int kc_count_dag_noalloc(uint32_t n, const uint64_t* d_orow, const uint32_t* d_o
 /* ---------------------------------------------------------------- serving
  * A request loop inside the library (no counterpart in the paper, which
  * runs one listing at a time): requests (a resident graph or an inline CSR,
- * and k) are queued by kc_serve_submit and taken by `lanes` worker threads.
- * Each lane owns its own device scratch and streams.  Whenever a lane is
- * free it takes every queued request that fits -- at most max_batch, and
- * only while the device bytes reserved by admitted, unfinished requests stay
- * within mem_cap_bytes -- and counts them together as one batch (the
- * kc_count_batched path).  Requests that arrive while a batch runs wait for
+ * k, and a mode: count, or list without keeping the tuples -- count and
+ * checksum) are queued by kc_serve_submit and taken by `lanes` worker
+ * threads.  Each lane owns its own device scratch and streams.  Whenever a
+ * lane is free it takes every queued request that fits -- at most max_batch,
+ * and only while the memory cap allows -- and enumerates them together (the
+ * kc_count_batched path: the batch's counts in one set of tier launches, its
+ * listings in another).  Requests that arrive while a batch runs wait for
  * the next free lane, so with two or more lanes batches overlap on the GPU.
  * A request's result is the same alone and in any mix.
+ *
+ * Device memory: mem_cap_bytes bounds what serving allocates (the resident
+ * graphs are the caller's and are not counted).  Admitted, unfinished
+ * requests may reserve half of it: a request's bytes bound what a batch
+ * allocates for it (root lists, heavy-root arena and task queue of its width
+ * tiers, an inline graph's upload).  The lanes' own scratch (memo tables and
+ * per-warp state, planned within cap / (2 lanes) each, at least one block of
+ * per-warp state per width tier) takes the other half; a lane that holds
+ * more than its share after a batch releases its scratch.  A request whose
+ * bytes exceed half the cap completes alone with KC_E_OOM.
  *
  * While serving, the context's resident graphs are read-only: do not call
  * kc_upload, kc_free_graph, kc_count, kc_list or kc_count_batched on it until
@@ -256,10 +274,12 @@ typedef struct kc_serve_opts {
   uint32_t lanes;          /* worker lanes (0: 2) */
   uint32_t max_batch;      /* requests per batch at most (0: 4096) */
   uint32_t reserved;
-  uint64_t mem_cap_bytes;  /* admission cap on reserved device bytes (0: 64 GiB) */
+  uint64_t mem_cap_bytes;  /* cap on the device bytes serving allocates (0: 64 GiB) */
 } kc_serve_opts;
 
-#define KC_SERVE_COUNT 0u      /* mode: count the k-cliques */
+#define KC_SERVE_COUNT 0u      /* mode: count the k-cliques (kc_count) */
+#define KC_SERVE_LIST 1u       /* mode: list the k-cliques without keeping them: count and checksum
+                                  (kc_list with cap = 0) */
 
 typedef struct kc_serve_result {
   uint64_t count;          /* k-cliques (when status == KC_OK) */
@@ -268,6 +288,9 @@ typedef struct kc_serve_result {
   uint64_t t_submit_ns;    /* steady-clock times: submission, batch start, completion */
   uint64_t t_start_ns;
   uint64_t t_done_ns;
+  uint64_t checksum;       /* KC_SERVE_LIST: kc_list's checksum of the k-cliques; KC_SERVE_COUNT: 0 */
+  uint32_t mode;           /* the request's mode */
+  uint32_t enumerated;     /* 1 if the GPU enumerated it, 0 if it was answered at submission */
 } kc_serve_result;
 
 typedef struct kc_serve_stats {
@@ -280,22 +303,27 @@ typedef struct kc_serve_stats {
   double mean_batch;       /* requests per batch */
   double req_per_s;        /* completed / (last completion - first submission) */
   double cliques_per_s;
-  uint64_t peak_reserved_bytes;
+  uint64_t peak_reserved_bytes; /* most device bytes held at once: admitted requests plus the lanes' scratch */
+  double p50_enum_ms;      /* latency percentiles of the requests the GPU enumerated (answered-at- */
+  double p99_enum_ms;      /* submission requests left out) */
+  uint64_t lane_scratch_bytes; /* device scratch the lanes hold now */
 } kc_serve_stats;
 
 /* Start serving on ctx (opts may be NULL).  KC_E_BUSY if already serving. */
 int kc_serve_start(kc_ctx* ctx, const kc_serve_opts* opts);
 
-/* Queue a count of the k-cliques of resident graph g; *ticket receives the
- * request's id.  mode must be KC_SERVE_COUNT.  Errors of the request itself
- * (k = 0, k > KC_MAX_K, unknown graph) are returned here. */
+/* Queue a request on resident graph g: mode KC_SERVE_COUNT counts the
+ * k-cliques (kc_count), KC_SERVE_LIST lists them without keeping the tuples
+ * (kc_list with cap = 0: count and checksum).  *ticket receives the
+ * request's id.  Errors of the request itself (k = 0, another mode,
+ * k > KC_MAX_K, unknown graph) are returned here. */
 int kc_serve_submit(kc_ctx* ctx, kc_graph g, uint32_t k, uint32_t mode, uint64_t* ticket);
 
 /* As kc_serve_submit for a graph given inline as a host CSR (same layout and
  * flags as kc_upload, KC_HOST_PTRS implied); the arrays are copied before
- * the call returns.  The lane uploads it, counts it and frees it; its device
- * bytes count against the admission cap until then.  A graph whose footprint
- * alone exceeds the cap completes with status KC_E_OOM. */
+ * the call returns.  The lane uploads it, enumerates it and frees it; its
+ * device bytes count against the cap until then.  A graph whose footprint
+ * alone exceeds half the cap completes with status KC_E_OOM. */
 int kc_serve_submit_csr(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr, const uint32_t* col, uint32_t flags,
                         uint32_t k, uint32_t mode, uint64_t* ticket);
 

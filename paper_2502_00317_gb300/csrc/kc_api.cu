@@ -20,37 +20,48 @@ int cuda_fail(kc_ctx* ctx, cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? KC_E_OOM : KC_E_CUDA;
 }
 
+// Scratch buffers come from the stream-ordered allocator on the stream of the
+// running call (ctx->cur_stream): a buffer that must grow is released after
+// the work already queued on that stream (which every launch that used it
+// was joined back into) instead of after a device-wide synchronisation, so
+// contexts that share the GPU (serving lanes) never wait for one another.
 int scratch_get(kc_ctx* ctx, int slot, size_t bytes, void** out) {
   if ((int)ctx->scratch.size() <= slot) ctx->scratch.resize(slot + 1);
   Scratch& sc = ctx->scratch[slot];
   if (bytes == 0) bytes = 16;
   if (sc.bytes < bytes) {
+    cudaStream_t s = ctx->cur_stream ? ctx->cur_stream : ctx->own_stream;
     if (sc.p) {
-      // earlier launches may still use the old buffer
-      KC_CUDA(cudaDeviceSynchronize());
-      KC_CUDA(cudaFree(sc.p));
+      KC_CUDA(cudaFreeAsync(sc.p, s));
+      ctx->scratch_bytes -= sc.bytes;
       sc.p = nullptr;
       sc.bytes = 0;
     }
     size_t want = bytes + bytes / 8;
-    KC_CUDA(cudaMalloc(&sc.p, want));
+    KC_CUDA(cudaMallocAsync(&sc.p, want, s));
     sc.bytes = want;
+    ctx->scratch_bytes += want;
+    ctx->scratch_peak = std::max(ctx->scratch_peak, ctx->scratch_bytes);
   }
   *out = sc.p;
   return KC_OK;
 }
 
-static void free_graph(DevGraph& g) {
-  cudaFree(g.core);
-  cudaFree(g.rank);
-  cudaFree(g.vert);
-  cudaFree(g.orow);
-  cudaFree(g.ocol);
+// Graph arrays come from the stream-ordered allocator too.  Every call that
+// read them synchronised its stream before returning, so they are released
+// in order on `s` without a device-wide synchronisation.
+static void free_graph(DevGraph& g, cudaStream_t s) {
+  for (void* p : {(void*)g.core, (void*)g.rank, (void*)g.vert, (void*)g.orow, (void*)g.ocol})
+    if (p) cudaFreeAsync(p, s);
+  cudaStreamSynchronize(s);
   g = DevGraph{};
 }
 
+// The stream of a call (the context's own when the caller passes NULL); it
+// also orders the call's scratch allocations.
 static cudaStream_t pick_stream(kc_ctx* ctx, void* stream) {
-  return stream ? (cudaStream_t)stream : ctx->own_stream;
+  ctx->cur_stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+  return ctx->cur_stream;
 }
 
 }  // namespace kc
@@ -91,6 +102,10 @@ int kc_create(kc_ctx** out, int device, const kc_opts* opts) {
     std::memcpy(&ctx->opts, opts, n);
   }
   ctx->opts.struct_size = sizeof(kc_opts);
+  if (ctx->opts.decomposition != KC_NODE_PARALLEL && ctx->opts.decomposition != KC_EDGE_PARALLEL) {
+    delete ctx;
+    return KC_E_INVALID_ARG;
+  }
   if (!ctx->opts.spin_limit) ctx->opts.spin_limit = 2000000000ull;  // 2 s, in nanoseconds
   ctx->device = device;
   auto fail = [&](cudaError_t e, const char* what) {
@@ -134,10 +149,11 @@ int kc_destroy(kc_ctx* ctx) {
   serve_release(ctx);
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
-  for (auto& kv : ctx->graphs) free_graph(kv.second);
+  for (auto& kv : ctx->graphs) free_graph(kv.second, ctx->own_stream);
   ctx->graphs.clear();
   for (auto& sc : ctx->scratch)
-    if (sc.p) cudaFree(sc.p);
+    if (sc.p) cudaFreeAsync(sc.p, ctx->own_stream);
+  if (ctx->own_stream) cudaStreamSynchronize(ctx->own_stream);
   ctx->scratch.clear();
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_acc) cudaFree(ctx->d_acc);
@@ -172,7 +188,7 @@ int kc_upload(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr, const uint32_t* c
   int st = prep_graph(ctx, n, rowptr, col, flags, &g, s);
   if (st != KC_OK) {
     cudaStreamSynchronize(s);
-    free_graph(g);
+    free_graph(g, s);
     return st;
   }
   uint32_t h = ctx->next_handle++;
@@ -187,8 +203,7 @@ int kc_free_graph(kc_ctx* ctx, kc_graph h) {
   auto it = ctx->graphs.find(h);
   if (it == ctx->graphs.end()) return KC_E_NOT_FOUND;
   KC_CUDA(cudaSetDevice(ctx->device));
-  KC_CUDA(cudaDeviceSynchronize());
-  free_graph(it->second);
+  free_graph(it->second, ctx->own_stream);
   ctx->graphs.erase(it);
   return KC_OK;
 }

@@ -121,26 +121,39 @@ static int plan_tier(kc_ctx* ctx, int t, int mode, uint32_t nroots, bool split, 
     tp->task_cap = std::min<uint64_t>((uint64_t)nroots * 32 * W, 1ull << 26);
   }
   if (!in_smem) {
-    uint64_t max_warps = std::max<uint64_t>(4, (1ull << 30) / wbytes);
+    // per-warp state in global memory: as many warps as the budget holds (at least one block)
+    const uint64_t gbudget = ctx->gstate_budget ? ctx->gstate_budget : (1ull << 30);
+    uint64_t max_warps = std::max<uint64_t>((uint64_t)tp->warps_per_block, gbudget / wbytes);
     blocks = std::max<uint64_t>(1, std::min<uint64_t>(blocks, max_warps / tp->warps_per_block));
     tp->gstate_bytes = wbytes;
   }
   tp->blocks = blocks;
   if (mode == 2) {
+    // per-warp memo tables within the budget (the tau of Sec. VI), shared by the tiers;
+    // a window of 32 slots is the smallest table, and a tier that cannot get one counts without
     uint64_t warps = blocks * tp->warps_per_block;
     uint32_t cap = 1u << 12;
     uint64_t budget = ctx->opts.memo_bytes ? ctx->opts.memo_bytes : (1ull << 30);
     uint64_t per_entry = 4 + 4ull * W + 8;
-    while (cap > 256 && warps * cap * per_entry > budget / kTiers) cap >>= 1;
-    tp->memo_cap = cap;
-    tp->memo_bytes = warps * cap * per_entry;
+    while (cap > 32 && warps * cap * per_entry > budget / kTiers) cap >>= 1;
+    if (warps * cap * per_entry > budget / kTiers) {
+      tp->mode = 0;
+      tier_kernels(t, 0, &tp->fn, &tp->fn_tasks);
+      if (tp->smem > 48 * 1024) {
+        KC_CUDA(cudaFuncSetAttribute(tp->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp->smem));
+        KC_CUDA(cudaFuncSetAttribute(tp->fn_tasks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp->smem));
+      }
+    } else {
+      tp->memo_cap = cap;
+      tp->memo_bytes = warps * cap * per_entry;
+    }
   }
   return KC_OK;
 }
 
 // Every tier in one mode; width 1 is never split (its roots are light).
-static int plan_all(kc_ctx* ctx, int mode, const uint32_t* hcnt, bool split, TierPlan* plans) {
-  for (int t = 0; t < kTiers; t++) KC_TRY(plan_tier(ctx, t, mode, hcnt[t], t > 0 && split, &plans[t]));
+static int plan_all(kc_ctx* ctx, int mode, const uint32_t* hcnt, bool split, bool edge, TierPlan* plans) {
+  for (int t = 0; t < kTiers; t++) KC_TRY(plan_tier(ctx, t, mode, hcnt[t], (t > 0 || edge) && split, &plans[t]));
   return KC_OK;
 }
 
@@ -158,9 +171,12 @@ static int launch_tiers(kc_ctx* ctx, const EnumKArgs& args, const uint32_t* hcnt
       ctx->opts.split_threshold == 0 ? kDefaultSplitWedges
       : (ctx->opts.split_threshold == 0xFFFFFFFFu ? 0u : ctx->opts.split_threshold);
   // the split path needs at least two levels below the first branch (k >= 5)
-  const bool split = split_wedges != 0 && split_ok;
+  // EdgeParallel decomposition (kc_opts.decomposition): every root of every
+  // tier is split into its first-level branches, for any k >= 3
+  const bool edge = ctx->opts.decomposition == KC_EDGE_PARALLEL;
+  const bool split = (split_wedges != 0 && split_ok) || edge;
   TierPlan plans[kTiers];
-  KC_TRY(plan_all(ctx, mode, hcnt, split, plans));
+  KC_TRY(plan_all(ctx, mode, hcnt, split, edge, plans));
   // one scratch region for every tier's global state, memo tables, arena and task queue
   uint64_t total = 0;
   uint64_t goff[kTiers], moff[kTiers], aoff[kTiers], toff[kTiers];
@@ -201,8 +217,9 @@ static int launch_tiers(kc_ctx* ctx, const EnumKArgs& args, const uint32_t* hcnt
       KC_CUDA(cudaMemsetAsync(x.memo_tags, 0, warps * tp.memo_cap * 4, ts));
     }
     if (tp.split) {
-      x.split_wedges = split_wedges;
+      x.split_wedges = split_ok ? split_wedges : 0u;
       x.split_min_d = 32;
+      x.edge_all = edge ? 1 : 0;
       x.arena = (uint8_t*)base + aoff[t];
       x.arena_units = tp.arena_units;
       x.arena_used = &ctx->d_acc[kAccArena0 + t];
@@ -231,6 +248,7 @@ static int launch_tiers(kc_ctx* ctx, const EnumKArgs& args, const uint32_t* hcnt
 }
 
 int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s) {
+  ctx->cur_stream = s;
   kc_stats stt{};
   uint32_t launches = 0, enum_launches = 0;
   uint32_t tier_roots[kTiers] = {0};
@@ -331,6 +349,7 @@ struct BinBatchArgs {
   uint32_t* roots_q;
   unsigned long long* acc;
   int pass;
+  uint32_t kmin;         // smallest k enumerated (3 counting: k <= 2 is answered on the host; 2 listing)
 };
 
 __global__ void k_bin_batch(BinBatchArgs a) {
@@ -351,7 +370,7 @@ __global__ void k_bin_batch(BinBatchArgs a) {
       r = (uint32_t)(g - a.qoff[q]);
       const BatchQuery bq = a.bq[q];
       const uint32_t d = (uint32_t)(bq.orow[r + 1] - bq.orow[r]);
-      if (bq.k >= 3 && d >= bq.k - 1) {
+      if (bq.k >= a.kmin && d >= bq.k - 1) {
         const uint32_t words = (d + 31) >> 5;
         t = 0;
         while (t < (uint32_t)kTiers && (uint32_t)tier_words((int)t) < words) t++;
@@ -374,7 +393,9 @@ __global__ void k_bin_batch(BinBatchArgs a) {
 }
 
 int run_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, bool memo, bool prune, uint64_t* counts,
-              cudaStream_t s) {
+              cudaStream_t s, uint64_t* checksums) {
+  const bool list = checksums != nullptr;
+  ctx->cur_stream = s;
   kc_stats stt{};
   uint32_t launches = 0, enum_launches = 0;
   cudaEvent_t* ev = ctx->ev;
@@ -392,14 +413,15 @@ int run_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, bool memo, bool pr
   const size_t obytes = (((size_t)nq + 1) * 8 + 255) & ~(size_t)255;
   const size_t cbytes = ((size_t)nq * 8 + 255) & ~(size_t)255;
   void* meta = nullptr;
-  KC_TRY(scratch_get(ctx, kScrBatch, qbytes + obytes + cbytes + 256, &meta));
+  KC_TRY(scratch_get(ctx, kScrBatch, qbytes + obytes + 2 * cbytes + 256, &meta));
   BatchQuery* d_q = (BatchQuery*)meta;
   uint64_t* d_off = (uint64_t*)((uint8_t*)meta + qbytes);
   unsigned long long* d_cnt = (unsigned long long*)((uint8_t*)meta + qbytes + obytes);
-  uint32_t* d_tc = (uint32_t*)((uint8_t*)meta + qbytes + obytes + cbytes);
+  unsigned long long* d_sum = (unsigned long long*)((uint8_t*)meta + qbytes + obytes + cbytes);
+  uint32_t* d_tc = (uint32_t*)((uint8_t*)meta + qbytes + obytes + 2 * cbytes);
   KC_CUDA(cudaMemcpyAsync(d_q, hq, (size_t)nq * sizeof(BatchQuery), cudaMemcpyHostToDevice, s));
   KC_CUDA(cudaMemcpyAsync(d_off, qoff.data(), ((size_t)nq + 1) * 8, cudaMemcpyHostToDevice, s));
-  KC_CUDA(cudaMemsetAsync(d_cnt, 0, (size_t)nq * 8, s));
+  KC_CUDA(cudaMemsetAsync(d_cnt, 0, 2 * cbytes, s));
   KC_CUDA(cudaMemsetAsync(d_tc, 0, 256, s));
   BinBatchArgs ba{};
   ba.bq = d_q;
@@ -408,6 +430,7 @@ int run_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, bool memo, bool pr
   ba.total = total;
   ba.cnts = d_tc;
   ba.acc = ctx->d_acc;
+  ba.kmin = list ? 2u : 3u;
   const unsigned bb =
       (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->num_sms * 8));
   uint32_t hcnt[16] = {0};
@@ -447,16 +470,20 @@ int run_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, bool memo, bool pr
     args.status = ctx->d_status;
     args.bq = d_q;
     args.bcount = d_cnt;
+    args.bsum = d_sum;
     uint32_t* troots[kTiers];
     uint32_t* troots_q[kTiers];
     for (int t = 0; t < kTiers; t++) {
       troots[t] = ba.roots + ba.tier_off[t];
       troots_q[t] = ba.roots_q + ba.tier_off[t];
     }
-    KC_TRY(launch_tiers(ctx, args, hcnt, troots, troots_q, memo ? 2 : 0, any5, s, &launches, &enum_launches));
+    // listing (cap 0: counts and checksums only) or counting, with the memo where allowed
+    const int mode = list ? 1 : (memo ? 2 : 0);
+    KC_TRY(launch_tiers(ctx, args, hcnt, troots, troots_q, mode, any5, s, &launches, &enum_launches));
   }
   KC_CUDA(cudaEventRecord(ev[7], s));
   KC_CUDA(cudaMemcpyAsync(counts, d_cnt, (size_t)nq * 8, cudaMemcpyDeviceToHost, s));
+  if (list) KC_CUDA(cudaMemcpyAsync(checksums, d_sum, (size_t)nq * 8, cudaMemcpyDeviceToHost, s));
   KC_CUDA(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc, kAccSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   KC_CUDA(cudaEventRecord(ev[8], s));
   KC_CUDA(cudaEventSynchronize(ev[8]));

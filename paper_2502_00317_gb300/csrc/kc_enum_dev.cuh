@@ -59,6 +59,7 @@ struct EnumKArgs {
   // split path (heavy roots): arena of published roots and a task queue
   uint32_t split_wedges;      // 0: never split
   int split_min_d;
+  int edge_all;               // EdgeParallel decomposition: every root's first-level branches are tasks
   uint8_t* arena;
   unsigned long long arena_units;  // 16-byte units
   unsigned long long* arena_used;
@@ -70,6 +71,7 @@ struct EnumKArgs {
   const BatchQuery* bq;         // nullptr: one graph (the fields above)
   const uint32_t* roots_q;      // [nroots] query of each root
   unsigned long long* bcount;   // [queries] counts
+  unsigned long long* bsum;     // [queries] listing checksums (list mode)
   uint32_t query;               // query bound to this copy of the arguments
 };
 
@@ -620,8 +622,10 @@ __device__ void dfs_plain(WarpState<W>& st, const EnumKArgs& a, int base, Acc& a
         if (!x) continue;
         bool mine = (x >> lane) & 1u;
         unsigned long long base_slot = 0;
-        if (lane == 0) base_slot = atomicAdd(&a.acc[kAccWritten], (unsigned long long)__popc(x));
-        base_slot = __shfl_sync(0xFFFFFFFFu, base_slot, 0);
+        if (a.cap) {  // cap 0: total and checksum only, no slots
+          if (lane == 0) base_slot = atomicAdd(&a.acc[kAccWritten], (unsigned long long)__popc(x));
+          base_slot = __shfl_sync(0xFFFFFFFFu, base_slot, 0);
+        }
         if (mine) {
           uint32_t id = a.vert[st.nbr[(w << 5) + lane]];
           unsigned long long slot = base_slot + __popc(x & lanemask_lt());
@@ -1074,6 +1078,9 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
     er = warp_sum(er);
     dense0 = 2ull * need * er > (unsigned long long)(need - 1) * d * d;
   }
+  // EdgeParallel (Sec. VII-D) as the whole decomposition: every root's
+  // first-level branches (u, v1) are tasks of the second phase
+  if (a.edge_all && need >= 2 && publish_root<W, MODE>(st, a, u, d, acc, d, dense0)) return;
   // heavy roots go to the split path: one task per first-level branch
   // dense roots keep their memo whole unless they are wide (more than 64 out-neighbours)
   if (a.split_wedges && d > a.split_min_d && (!dense0 || W >= 4) && need >= 4) {
@@ -1129,11 +1136,18 @@ __device__ __forceinline__ void bind_query(EnumKArgs& b, const EnumKArgs& a, uin
   b.query = q;
 }
 
-// A batch query's count so far, moved from the lanes' partials to its slot.
+// A batch query's count (and, listing, checksum) so far, moved from the
+// lanes' partials to its slots.
+template <int MODE>
 __device__ __forceinline__ void flush_query(const EnumKArgs& a, uint32_t q, Acc& acc) {
   const unsigned long long c = warp_sum(acc.cnt);
   acc.cnt = 0;
   if (lane_id() == 0 && c) atomicAdd(&a.bcount[q], c);
+  if (MODE == 1) {
+    const unsigned long long h = warp_sum(acc.sum);
+    acc.sum = 0;
+    if (lane_id() == 0 && h) atomicAdd(&a.bsum[q], h);
+  }
 }
 
 // Phase 1: one warp per root, roots taken from the tier's list.  With a batch
@@ -1154,12 +1168,12 @@ __global__ void __launch_bounds__(256) k_enum(const __grid_constant__ EnumKArgs 
     qi = __shfl_sync(0xFFFFFFFFu, qi, 0);
     if (qi >= a.nroots) break;
     const uint32_t u = a.roots[qi];
-    if (MODE != 1 && a.bq) {
+    if (a.bq) {
       const uint32_t q = a.roots_q[qi];
       EnumKArgs b = a;
       bind_query(b, a, q);
       root_body<W, MODE>(st, b, memo, &epoch, u, acc);
-      flush_query(a, q, acc);
+      flush_query<MODE>(a, q, acc);
     } else {
       root_body<W, MODE>(st, a, memo, &epoch, u, acc);
     }
@@ -1202,7 +1216,7 @@ __global__ void __launch_bounds__(256) k_tasks(const __grid_constant__ EnumKArgs
       u = hdr[0];
       d = (int)hdr[1];
       dense = hdr[3] != 0;
-      if (MODE != 1 && a.bq) {
+      if (a.bq) {
         bind_query(b, a, hdr[2]);
         need = b.k - 1;
       }
@@ -1230,7 +1244,7 @@ __global__ void __launch_bounds__(256) k_tasks(const __grid_constant__ EnumKArgs
     }
     // the kernel's own arguments are read in place; only a batch binds a copy
     run_branch<W, MODE>(st, a.bq ? b : a, memo, u, d, v1, acc, dense);
-    if (MODE != 1 && a.bq) flush_query(a, b.query, acc);
+    if (a.bq) flush_query<MODE>(a, b.query, acc);
     acc.ops64 += acc.ops;
     acc.ops = 0;
     __syncwarp();

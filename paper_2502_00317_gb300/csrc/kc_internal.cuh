@@ -107,6 +107,7 @@ struct DevGraph {
   uint32_t* vert = nullptr;   // [n] original id of each rank
   uint64_t* orow = nullptr;   // [n+1] DAG CSR in rank space
   uint32_t* ocol = nullptr;   // [m]
+  uint32_t tier_roots[kTiers] = {};  // vertices per bitmap-width tier (out-degree 1..32, 33..64, ...)
 };
 
 struct Scratch {
@@ -127,6 +128,10 @@ struct kc_ctx {
   uint32_t next_handle = 1;
   std::unordered_map<uint32_t, kc::DevGraph> graphs;
   std::vector<kc::Scratch> scratch;       // reusable device work buffers, by slot
+  uint64_t scratch_bytes = 0;             // bytes held by them now, and at most so far
+  uint64_t scratch_peak = 0;
+  uint64_t gstate_budget = 0;             // bytes for per-warp state in global memory per tier (0: 1 GiB)
+  cudaStream_t cur_stream = nullptr;      // stream of the running call (orders scratch allocations)
   uint32_t* d_status = nullptr;           // device status bits
   unsigned long long* d_acc = nullptr;    // device accumulators (count, checksum, written, stats ...)
   unsigned long long* h_acc = nullptr;    // pinned host mirror
@@ -219,6 +224,9 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& a, cudaStream_t s);
 
 // Batched counting (kc_enum.cu): one query per (graph, k); every query with
 // n > 0 and k >= 3 is counted in one set of tier launches into counts[q].
+// With checksums != nullptr the queries are listed instead (no tuples kept;
+// every query with n > 0 and k >= 2): counts[q] and checksums[q] are
+// kc_list's total and checksum.
 struct BatchQuery {
   const uint64_t* orow;  // the query graph's DAG (rank space)
   const uint32_t* ocol;
@@ -227,6 +235,6 @@ struct BatchQuery {
   uint32_t k;
 };
 int run_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, bool memo, bool prune, uint64_t* counts,
-              cudaStream_t s);
+              cudaStream_t s, uint64_t* checksums = nullptr);
 
 }  // namespace kc

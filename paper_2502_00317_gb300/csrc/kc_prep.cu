@@ -653,12 +653,16 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelArgs a) {
 
 // ================================================================= orient
 // DAG based on the order (Sec. II-A): keep (u, v) iff rank(u) < rank(v).
+// Also counts the vertices of each bitmap-width tier (out-degree 1..32,
+// 33..64, ..., 513..1024; wider ones in tier_hist[kTiers]), which bound the
+// scratch a count of the graph can need.
 __global__ void k_orient_count(const uint64_t* __restrict__ rowptr, const uint32_t* __restrict__ col, uint32_t n,
                                const uint32_t* __restrict__ rank, uint32_t* __restrict__ outdeg,
-                               uint32_t* __restrict__ max_out) {
+                               uint32_t* __restrict__ max_out, uint32_t* __restrict__ tier_hist) {
   const uint32_t lane = lane_id();
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  uint32_t hist = 0;  // lane t < kTiers + 1 counts tier t
   for (uint64_t v = gw; v < n; v += nw) {
     uint32_t rv = rank[v];
     uint32_t c = 0;
@@ -668,7 +672,14 @@ __global__ void k_orient_count(const uint64_t* __restrict__ rowptr, const uint32
       outdeg[rv] = c;
       atomicMax(max_out, c);
     }
+    if (c) {
+      const uint32_t words = (c + 31) >> 5;
+      uint32_t t = 0;
+      while (t < (uint32_t)kTiers && (1u << t) < words) t++;
+      hist += (lane == t);
+    }
   }
+  if (lane <= (uint32_t)kTiers && hist) atomicAdd(&tier_hist[lane], hist);
 }
 
 __global__ void k_orient_fill(const uint64_t* __restrict__ rowptr, const uint32_t* __restrict__ col, uint32_t n,
@@ -709,6 +720,7 @@ static unsigned grid_for_warps(kc_ctx* ctx, uint64_t warps, int threads) {
 
 int prep_graph(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr_in, const uint32_t* col_in, uint32_t flags,
                DevGraph* g, cudaStream_t s) {
+  ctx->cur_stream = s;
   kc_upload_stats st{};
   uint32_t launches = 0;
   cudaEvent_t* ev = ctx->ev;
@@ -730,7 +742,7 @@ int prep_graph(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr_in, const uint32_
   if (nnz) KC_CUDA(cudaMemcpyAsync(p_col, col_in, nnz * sizeof(uint32_t), kind, s));
   KC_CUDA(cudaEventRecord(ev[1], s));
 
-  uint32_t* d_small = nullptr;  // [0] status, [1] max_deg, [2] max_out, [3..4] peel result
+  uint32_t* d_small = nullptr;  // [0] status, [1] max_deg, [2] max_out, [3..4] peel result, [8..14] tier counts
   KC_TRY(scratch_get(ctx, kScrC, 64, (void**)&d_small));
   KC_CUDA(cudaMemsetAsync(d_small, 0, 64, s));
   uint32_t* d_status = d_small;
@@ -794,7 +806,7 @@ int prep_graph(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr_in, const uint32_
     launches++;
   }
   KC_CUDA(cudaEventRecord(ev[2], s));
-  uint32_t h_small[8] = {0};
+  uint32_t h_small[16] = {0};
   KC_CUDA(cudaMemcpyAsync(h_small, d_small, sizeof(h_small), cudaMemcpyDeviceToHost, s));
   KC_CUDA(cudaStreamSynchronize(s));
   if (h_small[0] & kStBadGraph) return KC_E_INVALID_GRAPH;
@@ -803,11 +815,11 @@ int prep_graph(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr_in, const uint32_
   // ---- allocate the graph's own arrays
   g->n = n;
   g->m = nnz / 2;
-  KC_CUDA(cudaMalloc(&g->core, std::max<uint64_t>(n, 1) * sizeof(uint32_t)));
-  KC_CUDA(cudaMalloc(&g->rank, std::max<uint64_t>(n, 1) * sizeof(uint32_t)));
-  KC_CUDA(cudaMalloc(&g->vert, std::max<uint64_t>(n, 1) * sizeof(uint32_t)));
-  KC_CUDA(cudaMalloc(&g->orow, (n + 1ull) * sizeof(uint64_t)));
-  KC_CUDA(cudaMalloc(&g->ocol, std::max<uint64_t>(g->m, 1) * sizeof(uint32_t)));
+  KC_CUDA(cudaMallocAsync(&g->core, std::max<uint64_t>(n, 1) * sizeof(uint32_t), s));
+  KC_CUDA(cudaMallocAsync(&g->rank, std::max<uint64_t>(n, 1) * sizeof(uint32_t), s));
+  KC_CUDA(cudaMallocAsync(&g->vert, std::max<uint64_t>(n, 1) * sizeof(uint32_t), s));
+  KC_CUDA(cudaMallocAsync(&g->orow, (n + 1ull) * sizeof(uint64_t), s));
+  KC_CUDA(cudaMallocAsync(&g->ocol, std::max<uint64_t>(g->m, 1) * sizeof(uint32_t), s));
 
   // ---- peel (one cooperative launch)
   if (n > 0) {
@@ -849,7 +861,7 @@ int prep_graph(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr_in, const uint32_
   // ---- orient
   uint32_t* outdeg = frontier;  // reuse (peel is done with it)
   if (n > 0) {
-    k_orient_count<<<wgrid, 256, 0, s>>>(rowptr, col, n, g->rank, outdeg, d_maxout);
+    k_orient_count<<<wgrid, 256, 0, s>>>(rowptr, col, n, g->rank, outdeg, d_maxout, d_small + 8);
     KC_CUDA(cudaGetLastError());
     launches++;
   }
@@ -865,6 +877,7 @@ int prep_graph(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr_in, const uint32_
   g->max_out = h_small[2];
   g->degeneracy = h_small[3];
   g->peel_rounds = h_small[4];
+  for (int t = 0; t < kTiers; t++) g->tier_roots[t] = h_small[8 + t];
   KC_TRY(segmented_sort(ctx, g->ocol, g->orow, n, g->m, g->max_out, nullptr, s, &launches));
   KC_CUDA(cudaEventRecord(ev[4], s));
   KC_CUDA(cudaEventSynchronize(ev[4]));

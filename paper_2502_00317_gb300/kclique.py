@@ -43,6 +43,10 @@ EXPORTS = (
 )
 
 KC_SERVE_COUNT = 0
+KC_SERVE_LIST = 1
+
+KC_NODE_PARALLEL = 0
+KC_EDGE_PARALLEL = 1
 
 
 class KcError(RuntimeError):
@@ -60,6 +64,8 @@ class kc_opts(ctypes.Structure):
         ("split_threshold", ctypes.c_uint32),
         ("memo_bytes", ctypes.c_uint64),
         ("spin_limit", ctypes.c_uint64),
+        ("decomposition", ctypes.c_uint32),
+        ("reserved0", ctypes.c_uint32),
     ]
 
 
@@ -123,6 +129,9 @@ class kc_serve_result(ctypes.Structure):
         ("t_submit_ns", ctypes.c_uint64),
         ("t_start_ns", ctypes.c_uint64),
         ("t_done_ns", ctypes.c_uint64),
+        ("checksum", ctypes.c_uint64),
+        ("mode", ctypes.c_uint32),
+        ("enumerated", ctypes.c_uint32),
     ]
 
 
@@ -138,6 +147,9 @@ class kc_serve_stats(ctypes.Structure):
         ("req_per_s", ctypes.c_double),
         ("cliques_per_s", ctypes.c_double),
         ("peak_reserved_bytes", ctypes.c_uint64),
+        ("p50_enum_ms", ctypes.c_double),
+        ("p99_enum_ms", ctypes.c_double),
+        ("lane_scratch_bytes", ctypes.c_uint64),
     ]
 
 
@@ -217,9 +229,9 @@ def kc_strerror(status: int) -> str:
 
 
 def kc_create(device: int = 0, no_memo: bool = False, no_prune: bool = False, memo_bytes: int = 0,
-              spin_limit: int = 0, split_threshold: int = 0) -> int:
+              spin_limit: int = 0, split_threshold: int = 0, decomposition: int = 0) -> int:
     o = kc_opts(ctypes.sizeof(kc_opts), int(no_memo), int(no_prune), int(split_threshold), int(memo_bytes),
-                int(spin_limit))
+                int(spin_limit), int(decomposition), 0)
     h = ctypes.c_void_p()
     _check(load().kc_create(ctypes.byref(h), int(device), ctypes.byref(o)), "kc_create")
     return h.value

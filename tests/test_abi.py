@@ -72,12 +72,21 @@ def test_create_fails_cleanly_without_gpu():
     assert not h.value
 
 
-def test_struct_sizes_match_header():
-    # kc_opts: 4 x u32 + 2 x u64 = 32 bytes; kc_stats: 3 f32 + 2 u32 + 8 u64 + 6 f32 + 6 u32 + 1 u64 = 144 bytes
-    assert ctypes.sizeof(kc.kc_opts) == 32
-    assert ctypes.sizeof(kc.kc_graph_info) == 24
-    assert ctypes.sizeof(kc.kc_stats) == 144
-    assert ctypes.sizeof(kc.kc_upload_stats) == 24
-    assert ctypes.sizeof(kc.kc_serve_opts) == 24
-    assert ctypes.sizeof(kc.kc_serve_result) == 40
-    assert ctypes.sizeof(kc.kc_serve_stats) == 80
+def test_struct_sizes_match_header(tmp_path):
+    """The ctypes mirrors have the layout the C compiler gives the header's structs."""
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    names = ["kc_opts", "kc_graph_info", "kc_stats", "kc_upload_stats", "kc_serve_opts", "kc_serve_result",
+             "kc_serve_stats"]
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "kclique.h"\nint main(void) {\n' +
+                   "".join(f'  printf("%zu\\n", sizeof({n}));\n' for n in names) + "  return 0;\n}\n")
+    exe = tmp_path / "sizes"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    for n, size in zip(names, got):
+        assert ctypes.sizeof(getattr(kc, n)) == size, n

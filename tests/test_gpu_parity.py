@@ -236,6 +236,45 @@ def test_split_path_matches_oracle(maker, splits):
             c.close()
 
 
+@pytest.mark.parametrize("maker", [
+    lambda: gg.chung_lu_planted(n=20000, n_cliques=40, seed=1),
+    lambda: gg.rgg_torus(4000, 70.0, seed=6),
+    lambda: gg.er_gnp(400, 0.3, 12),
+    lambda: gg.complete(70),
+])
+def test_edge_parallel_decomposition_matches_oracle(maker):
+    """EdgeParallel as the whole decomposition (Sec. VII-D): every root's
+    first-level branches (u, v) are separate tasks of the second launch, in
+    every width tier; counts with and without the memo, checksums and the
+    listed tuples equal the oracle's."""
+    g = maker()
+    og = oracle.OracleGraph.from_graph(g)
+    ctxs = [kc.Context(0, decomposition=kc.KC_EDGE_PARALLEL),
+            kc.Context(0, decomposition=kc.KC_EDGE_PARALLEL, no_memo=True)]
+    try:
+        hs = [c.upload_host(g.n, g.rowptr, g.col) for c in ctxs]
+        for k in (3, 4, 5, 6, 7):
+            want = og.count(k)[0]
+            for c, h in zip(ctxs, hs):
+                assert c.count(h, k) == want, (k, c.stats())
+                st = c.stats()
+                if want:  # every root that survives pruning was split into its branches
+                    assert st["roots_heavy"] == st["roots_total"] - st["roots_pruned"] > 0, st
+        for k in (3, 5):
+            assert ctxs[0].list(hs[0], k, None, 0)[1:] == og.checksum(k), k
+        want4 = og.count(4)[0]
+        if want4 <= 300000:
+            arr, t, s = _list_all(ctxs[0], hs[0], 4, want4)
+            assert (t, s) == og.checksum(4)
+            assert np.array_equal(np.unique(arr, axis=0), np.unique(og.list(4)[0], axis=0))
+    finally:
+        for c in ctxs:
+            c.close()
+    with pytest.raises(kc.KcError) as e:
+        kc.Context(0, decomposition=7)
+    assert e.value.status == kc.KC_E_INVALID_ARG
+
+
 # ------------------------------------------------- peel / orient (a2, a3)
 @pytest.mark.parametrize("maker", [
     lambda: gg.er_gnp(3000, 0.004, 7),

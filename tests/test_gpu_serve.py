@@ -1,9 +1,11 @@
 """Serving (kc_serve_*): continuous batching must not change any result.
 
-Each request's count must equal kc_count on the same graph alone, whatever
-mix of requests it was batched with; the memory-admission cap must hold; a
-request too large for the cap fails alone; stopping ends every request.
-Counts are exact integers, so "the same" is equality.
+Each request's count (and, for listing requests, checksum) must equal
+kc_count / kc_list on the same graph alone, whatever mix of requests it was
+batched with; the memory cap must hold, for what serving reserves and for
+the device memory it really takes; a request too large for the cap fails
+alone; stopping ends every request.  Counts and checksums are exact
+integers, so "the same" is equality.
 """
 import threading
 
@@ -30,10 +32,13 @@ def _graphs():
 
 
 def _expected(c, hs, ks):
+    """(count, checksum) of every (graph, k) alone: kc_count and kc_list with cap 0."""
     table = {}
     for h in set(hs):
         for k in set(ks):
-            table[(h, k)] = c.count(h, k)
+            _, total, checksum = c.list(h, k, None, 0)
+            assert total == c.count(h, k)
+            table[(h, k)] = (total, checksum)
     return table
 
 
@@ -45,12 +50,15 @@ def test_results_same_alone_and_in_the_mix():
         want = _expected(c, hs, ks)
         kc.kc_serve_start(c.h, lanes=2, max_batch=64)
         rng = np.random.default_rng(0)
-        reqs = [(int(hs[i]), int(ks[j])) for i, j in zip(rng.integers(0, len(hs), 400), rng.integers(0, len(ks), 400))]
+        n_req = 400
+        modes = rng.integers(0, 2, n_req)
+        reqs = [(int(hs[i]), int(ks[j]), int(md)) for i, j, md in
+                zip(rng.integers(0, len(hs), n_req), rng.integers(0, len(ks), n_req), modes)]
         tickets = [None] * len(reqs)
 
         def submit(lo, hi):
             for i in range(lo, hi):
-                tickets[i] = kc.kc_serve_submit(c.h, *reqs[i])
+                tickets[i] = kc.kc_serve_submit(c.h, reqs[i][0], reqs[i][1], reqs[i][2])
 
         ths = [threading.Thread(target=submit, args=(i * 100, (i + 1) * 100)) for i in range(4)]
         for t in ths:
@@ -58,16 +66,19 @@ def test_results_same_alone_and_in_the_mix():
         for t in ths:
             t.join()
         sizes = []
-        for (h, k), t in zip(reqs, tickets):
+        for (h, k, mode), t in zip(reqs, tickets):
             r = kc.kc_serve_wait(c.h, t, 120000)
             assert r is not None and r["status"] == kc.KC_OK, r
-            assert r["count"] == want[(h, k)], (h, k)
+            assert r["mode"] == mode
+            assert r["count"] == want[(h, k)][0], (h, k, mode)
+            assert r["checksum"] == (want[(h, k)][1] if mode == kc.KC_SERVE_LIST else 0), (h, k, mode)
             assert r["t_submit_ns"] <= r["t_start_ns"] <= r["t_done_ns"]
             sizes.append(r["batch_size"])
         assert max(sizes) > 1  # requests really were batched together
         st = kc.kc_serve_stats_get(c.h)
         assert st["submitted"] == st["completed"] == len(reqs) and st["failed"] == 0
         assert st["p50_ms"] <= st["p99_ms"]
+        assert st["p50_enum_ms"] <= st["p99_enum_ms"]
         with pytest.raises(kc.KcError) as e:  # collected already
             kc.kc_serve_poll(c.h, tickets[0])
         assert e.value.status == kc.KC_E_NOT_FOUND
@@ -77,33 +88,59 @@ def test_results_same_alone_and_in_the_mix():
 
 
 def test_inline_graphs_and_admission_cap():
+    import threading as th
+
+    import torch
+
     graphs = _graphs()
+    cap = 256 << 20
     with kc.Context(0) as c:
         hs = [c.upload_host(g.n, g.rowptr, g.col) for g in graphs]
-        big = graphs[3]
-        # the cap admits the largest inline graph alone, so inline requests wait for one another
-        cap = 48 * big.n + 8 * big.nnz + 8 * big.n + 1024
+        # an inline graph whose upload alone needs more than half the cap fails alone
+        huge = gg.er_gnm(2_000_000, 4_000_000, seed=1)
+        raw = gg.rmat(scale=10, edge_factor=8, seed=4)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        low = [free0]
+        stop = th.Event()
+
+        def watch():  # device memory actually taken while serving
+            while not stop.is_set():
+                low[0] = min(low[0], torch.cuda.mem_get_info()[0])
+                stop.wait(0.002)
+
+        w = th.Thread(target=watch)
+        w.start()
         kc.kc_serve_start(c.h, lanes=2, max_batch=16, mem_cap_bytes=cap)
         jobs = []
         for i, g in enumerate(graphs):
             for k in (3, 5, 7):
-                jobs.append((kc.kc_serve_submit_csr(c.h, g.n, g.rowptr, g.col, k), g, k))
-                jobs.append((kc.kc_serve_submit(c.h, hs[i], k), g, k))
+                for mode in (kc.KC_SERVE_COUNT, kc.KC_SERVE_LIST):
+                    jobs.append((kc.kc_serve_submit_csr(c.h, g.n, g.rowptr, g.col, k, mode=mode), g, k, mode))
+                    jobs.append((kc.kc_serve_submit(c.h, hs[i], k, mode), g, k, mode))
         # a raw CSR that the lane must canonicalise
-        raw = gg.rmat(scale=10, edge_factor=8, seed=4)
-        jobs.append((kc.kc_serve_submit_csr(c.h, raw.n, raw.rowptr, raw.col, 4, canonicalize=True), raw, 4))
-        # an inline graph larger than the cap fails alone
-        huge = gg.er_gnm(200000, 400000, seed=1)
+        jobs.append((kc.kc_serve_submit_csr(c.h, raw.n, raw.rowptr, raw.col, 4, canonicalize=True), raw, 4, 0))
+        jobs.append((kc.kc_serve_submit_csr(c.h, raw.n, raw.rowptr, raw.col, 4, canonicalize=True,
+                                            mode=kc.KC_SERVE_LIST), raw, 4, 1))
         t_huge = kc.kc_serve_submit_csr(c.h, huge.n, huge.rowptr, huge.col, 3)
-        for t, g, k in jobs:
+        oracles = {}
+        for t, g, k, mode in jobs:
             r = kc.kc_serve_wait(c.h, t, 120000)
             assert r["status"] == kc.KC_OK
-            assert r["count"] == oracle.OracleGraph.from_graph(g).count(k)[0], (g.name, k)
+            og = oracles.setdefault(id(g), oracle.OracleGraph.from_graph(g))
+            want = og.checksum(k)
+            assert r["count"] == want[0], (g.name, k)
+            assert r["checksum"] == (want[1] if mode == kc.KC_SERVE_LIST else 0), (g.name, k)
         r = kc.kc_serve_wait(c.h, t_huge, 120000)
         assert r["status"] == kc.KC_E_OOM
         st = kc.kc_serve_stats_get(c.h)
-        assert 0 < st["peak_reserved_bytes"] <= cap
         kc.kc_serve_stop(c.h)
+        stop.set()
+        w.join()
+        assert 0 < st["peak_reserved_bytes"] <= cap
+        # what the device really lost while serving: the cap, plus the lanes' fixed
+        # records (streams, events, accumulators) and the allocator's rounding
+        assert free0 - low[0] <= cap + (32 << 20), (free0 - low[0], cap)
         for h in hs:
             c.free(h)
 
@@ -121,7 +158,7 @@ def test_stop_ends_every_request_and_errors():
             kc.kc_serve_start(c.h)
         assert e.value.status == kc.KC_E_BUSY
         for bad, code in (((h, 0), kc.KC_E_INVALID_ARG), ((h + 77, 4), kc.KC_E_NOT_FOUND),
-                          ((h, kc.KC_MAX_K + 1), kc.KC_E_UNSUPPORTED)):
+                          ((h, kc.KC_MAX_K + 1), kc.KC_E_UNSUPPORTED), ((h, 4, 7), kc.KC_E_INVALID_ARG)):
             with pytest.raises(kc.KcError) as e:
                 kc.kc_serve_submit(c.h, *bad)
             assert e.value.status == code

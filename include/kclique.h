@@ -96,7 +96,11 @@ typedef struct kc_stats {
   uint64_t memo_frames;    /* memoised frames opened (device trie walks) */
   float ms_tier[6];        /* device time of each width tier (1, 2, 4, 8, 16, 32 words) */
   uint32_t roots_tier[6];  /* roots in each width tier */
-  uint64_t word_ops;       /* 32-bit candidate words intersected (AND + POPC) by the enumerator */
+  uint64_t word_ops;       /* 32-bit candidate words intersected (AND + POPC) by the enumerator, plus the
+                              words of the narrow bit-matrices built for branches */
+  uint64_t warp_ns_build;  /* summed over warps: nanoseconds spent building root bit-matrices (a5) */
+  uint64_t warp_ns_busy;   /* summed over warps: nanoseconds spent on roots and tasks in all */
+  uint64_t memo_peak;      /* most trie entries stored for one root (the size the paper bounds by tau) */
 } kc_stats;
 
 /* Per-stage device times of the last kc_upload (CUDA events). */
@@ -303,7 +307,8 @@ typedef struct kc_serve_stats {
   double mean_batch;       /* requests per batch */
   double req_per_s;        /* completed / (last completion - first submission) */
   double cliques_per_s;
-  uint64_t peak_reserved_bytes; /* most device bytes held at once: admitted requests plus the lanes' scratch */
+  uint64_t peak_reserved_bytes; /* most device bytes reserved at once: admitted requests plus the lanes'
+                              scratch budgets (at most mem_cap_bytes) */
   double p50_enum_ms;      /* latency percentiles of the requests the GPU enumerated (answered-at- */
   double p99_enum_ms;      /* submission requests left out) */
   uint64_t lane_scratch_bytes; /* device scratch the lanes hold now */

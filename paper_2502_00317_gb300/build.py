@@ -42,7 +42,7 @@ def _digest() -> str:
         if os.path.isfile(p):
             h.update(name.encode())
             h.update(open(p, "rb").read())
-    h.update(" ".join(_flags()).encode())
+    h.update(" ".join(_flags() + ["-rdc=true"]).encode())
     return h.hexdigest()
 
 
@@ -71,7 +71,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *_flags(extra_flags), "-c", os.path.join(CSRC, src), "-o", obj]
+        # relocatable device code: each width's searches are compiled once, in
+        # its own unit, and called from the kernels of every other width
+        cmd = [cc, *_flags(extra_flags), "-rdc=true", "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -82,7 +84,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [cc, *ARCH, "-shared", "-rdc=true", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -67,6 +67,9 @@ struct TierPlan {
   size_t smem = 0;
   uint64_t blocks = 0;
   uint64_t gstate_bytes = 0;   // per-warp state in global memory (0: in shared memory)
+  uint32_t depth = 0;          // stack depth of the per-warp states
+  uint32_t sstride = 0;        // shared-memory bytes per warp
+  uint32_t coff = 0;           // offset of the narrow branch state in them
   uint32_t memo_cap = 0;       // entries per warp (0: no memo)
   uint64_t memo_bytes = 0;
   bool split = false;          // heavy roots of this tier go to the split path
@@ -93,17 +96,20 @@ static void tier_kernels(int t, int mode, const void** fe, const void** ft) {
   }
 }
 
-static int plan_tier(kc_ctx* ctx, int t, int mode, uint32_t nroots, bool split, TierPlan* tp) {
+static int plan_tier(kc_ctx* ctx, int t, int mode, uint32_t nroots, bool split, uint32_t depth, TierPlan* tp) {
   const int W = tier_words(t);
-  const size_t wbytes = warp_state_stride(W);
+  const size_t wbytes = warp_state_stride(W, (int)depth);
   const bool in_smem = W <= 8;
   tp->W = W;
   tp->mode = mode;
   tp->nroots = nroots;
+  tp->depth = depth;
+  tp->sstride = (uint32_t)warp_smem_bytes(W, (int)depth);
+  tp->coff = in_smem ? (uint32_t)wbytes : 0u;
   tier_kernels(t, mode, &tp->fn, &tp->fn_tasks);
   if (nroots == 0) return KC_OK;
   tp->warps_per_block = W <= 4 ? 8 : 4;
-  tp->smem = in_smem ? wbytes * tp->warps_per_block : 0;
+  tp->smem = (size_t)tp->sstride * tp->warps_per_block;
   if (tp->smem > 48 * 1024) {
     KC_CUDA(cudaFuncSetAttribute(tp->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp->smem));
     KC_CUDA(cudaFuncSetAttribute(tp->fn_tasks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp->smem));
@@ -152,8 +158,10 @@ static int plan_tier(kc_ctx* ctx, int t, int mode, uint32_t nroots, bool split, 
 }
 
 // Every tier in one mode; width 1 is never split (its roots are light).
-static int plan_all(kc_ctx* ctx, int mode, const uint32_t* hcnt, bool split, bool edge, TierPlan* plans) {
-  for (int t = 0; t < kTiers; t++) KC_TRY(plan_tier(ctx, t, mode, hcnt[t], (t > 0 || edge) && split, &plans[t]));
+static int plan_all(kc_ctx* ctx, int mode, const uint32_t* hcnt, bool split, bool edge, uint32_t depth,
+                    TierPlan* plans) {
+  for (int t = 0; t < kTiers; t++)
+    KC_TRY(plan_tier(ctx, t, mode, hcnt[t], (t > 0 || edge) && split, depth, &plans[t]));
   return KC_OK;
 }
 
@@ -176,7 +184,7 @@ static int launch_tiers(kc_ctx* ctx, const EnumKArgs& args, const uint32_t* hcnt
   const bool edge = ctx->opts.decomposition == KC_EDGE_PARALLEL;
   const bool split = (split_wedges != 0 && split_ok) || edge;
   TierPlan plans[kTiers];
-  KC_TRY(plan_all(ctx, mode, hcnt, split, edge, plans));
+  KC_TRY(plan_all(ctx, mode, hcnt, split, edge, args.depth, plans));
   // one scratch region for every tier's global state, memo tables, arena and task queue
   uint64_t total = 0;
   uint64_t goff[kTiers], moff[kTiers], aoff[kTiers], toff[kTiers];
@@ -199,6 +207,8 @@ static int launch_tiers(kc_ctx* ctx, const EnumKArgs& args, const uint32_t* hcnt
     cudaStream_t ts = ctx->tier_stream[t];
     KC_CUDA(cudaStreamWaitEvent(ts, ctx->ev_fork, 0));
     EnumKArgs x = args;
+    x.sstride = tp.sstride;
+    x.coff = tp.coff;
     x.roots = troots[t];
     x.roots_q = troots_q ? troots_q[t] : nullptr;
     x.nroots = tp.nroots;
@@ -292,6 +302,7 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
     args.ocol = g.ocol;
     args.vert = g.vert;
     args.k = k;
+    args.depth = k + 1;
     args.prune = ea.prune ? 1 : 0;
     args.memo = ea.memo ? 1 : 0;
     args.out = ea.d_buf;
@@ -321,6 +332,9 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
   stt.memo_frames = ctx->h_acc[kAccMemoFrames];
   stt.roots_heavy = ctx->h_acc[kAccRootsHeavy];
   stt.word_ops = ctx->h_acc[kAccWordOps];
+  stt.warp_ns_build = ctx->h_acc[kAccBuildNs];
+  stt.warp_ns_busy = ctx->h_acc[kAccBusyNs];
+  stt.memo_peak = ctx->h_acc[kAccMemoPeak];
   if (k >= 2) {
     for (int t = 0; t < kTiers; t++) {
       stt.roots_tier[t] = tier_roots[t];
@@ -464,6 +478,9 @@ int run_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, bool memo, bool pr
   if (nroots) {
     EnumKArgs args{};
     args.k = 3;  // per query through bq; this value is never used for a root
+    uint32_t kmax = 3;
+    for (uint32_t q = 0; q < nq; q++) kmax = std::max(kmax, hq[q].k);
+    args.depth = kmax + 1;  // stacks deep enough for every query
     args.prune = prune ? 1 : 0;
     args.memo = memo ? 1 : 0;
     args.acc = ctx->d_acc;
@@ -501,6 +518,9 @@ int run_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, bool memo, bool pr
   stt.memo_full = ctx->h_acc[kAccMemoFull];
   stt.memo_frames = ctx->h_acc[kAccMemoFrames];
   stt.word_ops = ctx->h_acc[kAccWordOps];
+  stt.warp_ns_build = ctx->h_acc[kAccBuildNs];
+  stt.warp_ns_busy = ctx->h_acc[kAccBusyNs];
+  stt.memo_peak = ctx->h_acc[kAccMemoPeak];
   for (int t = 0; t < kTiers; t++) {
     stt.roots_tier[t] = hcnt[t];
     if (hcnt[t]) cudaEventElapsedTime(&stt.ms_tier[t], ctx->ev_tier0[t], ctx->ev_tier1[t]);
@@ -580,13 +600,16 @@ int static_tier(int t, int num_sms, const EnumKArgs& x, cudaStream_t s) {
   const void* ft = nullptr;
   tier_kernels(t, 0, &fe, &ft);
   const int wpb = W <= 4 ? 8 : 4;
-  const size_t smem = warp_state_stride(W) * wpb;
+  const size_t sstride = warp_smem_bytes(W, (int)x.depth);
+  const size_t smem = sstride * wpb;
   if (smem > 48 * 1024) KC_CUDA(cudaFuncSetAttribute(fe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fe, wpb * 32, smem));
   uint64_t blocks = (uint64_t)num_sms * std::max(per_sm, 1);
   blocks = std::max<uint64_t>(1, std::min<uint64_t>(blocks, (x.nroots + wpb - 1) / wpb));
   EnumKArgs y = x;
+  y.sstride = (uint32_t)sstride;
+  y.coff = (uint32_t)warp_state_stride(W, (int)x.depth);
   void* kargs[] = {&y};
   KC_CUDA(cudaLaunchKernel(fe, dim3((unsigned)blocks), dim3(wpb * 32), kargs, smem, s));
   return KC_OK;
@@ -643,6 +666,7 @@ extern "C" int kc_count_dag_noalloc(uint32_t n, const uint64_t* d_orow, const ui
   // no id map: the count kernel (mode 0) never reads vert, only listing does
   x.vert = nullptr;
   x.k = k;
+  x.depth = k + 1;
   x.prune = 1;
   x.acc = acc;
   x.status = status;

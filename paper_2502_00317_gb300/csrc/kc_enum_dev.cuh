@@ -73,56 +73,70 @@ struct EnumKArgs {
   unsigned long long* bcount;   // [queries] counts
   unsigned long long* bsum;     // [queries] listing checksums (list mode)
   uint32_t query;               // query bound to this copy of the arguments
+  // layout of the per-warp state
+  uint32_t depth;               // D: stack depth of every state (k + 1, the batch's largest k + 1)
+  uint32_t sstride;             // shared-memory bytes per warp
+  uint32_t coff;                // offset of the narrow branch state in the warp's shared memory
 };
 
-// Bytes of one warp's working state at width W (the layout of WarpState::carve).
-__host__ __device__ constexpr size_t warp_state_raw(int W) {
-  return (size_t)32 * W * 4 + (size_t)32 * W * W * 4 + (size_t)KMAX * W * 4 * 2 + (size_t)KMAX * 8 +
-         (size_t)KMAX * 4 * 2 + (size_t)(KMAX + 1) * 4 + KMAX + 32 * W + KMAX * 2 + 16 + 32 * 4;
+// Bytes of one warp's working state at width W with stacks of depth D (the
+// layout of WarpState::carve; D = k + 1 covers every depth of a k-clique search).
+__host__ __device__ constexpr size_t warp_state_raw(int W, int D) {
+  return (size_t)D * 8 + 32 * 4 + (size_t)32 * W * 4 + (size_t)32 * W * W * 4 + (size_t)D * W * 4 * 2 +
+         (size_t)D * 4 * 2 + (size_t)(D + 1) * 4 + (size_t)32 * W * 2 + D + 32 * W + D + D;
 }
 
 // Per-warp stride of that state (16-byte aligned).
-__host__ __device__ constexpr size_t warp_state_stride(int W) { return (warp_state_raw(W) + 15) & ~(size_t)15; }
+__host__ __device__ constexpr size_t warp_state_stride(int W, int D) { return (warp_state_raw(W, D) + 15) & ~(size_t)15; }
+
+// Width of the narrow bit-matrix a branch of a width-W root is re-indexed
+// into when its candidate set is small (0: none).  The narrow state lives in
+// shared memory after the root's own.
+__host__ __device__ constexpr int compact_width(int W) { return W >= 16 ? 8 : W / 2; }
+
+// Shared-memory bytes per warp of a width-W kernel: the root's state (widths
+// up to 8; wider ones keep it in global memory) and the narrow branch state.
+__host__ __device__ constexpr size_t warp_smem_bytes(int W, int D) {
+  return (W <= 8 ? warp_state_stride(W, D) : 0) + (compact_width(W) ? warp_state_stride(compact_width(W), D) : 0);
+}
 
 // Per-warp working state, carved from shared or global memory.
 template <int W>
 struct WarpState {
   uint32_t* nbr;              // [32W] ranks of N+(u), ascending
   uint32_t* rows;             // [32W*W] bit-matrix rows
-  uint32_t* masks;            // [KMAX*W] masks[l*W+w]: local vertices with r >= l
-  uint32_t* cand;             // [KMAX*W] candidate set per depth
-  unsigned long long* sum;    // [KMAX] frame partial counts (memo variant)
-  int32_t* pos;               // [KMAX] next pick position (descending), -1 when done
-  int32_t* cur;               // [KMAX] vertex whose child frame is open
-  uint32_t* sid;              // [KMAX+1] sorted original ids of the open clique prefix
-  uint8_t* sins;              // [KMAX] insertion index of each pick in sid
+  uint32_t* masks;            // [D*W] masks[l*W+w]: local vertices with r >= l
+  uint32_t* cand;             // [D*W] candidate set per depth
+  unsigned long long* sum;    // [D] frame partial counts (memo variant)
+  int32_t* pos;               // [D] next pick position (descending), -1 when done
+  int32_t* cur;               // [D] vertex whose child frame is open
+  uint32_t* sid;              // [D+1] sorted original ids of the open clique prefix
+  uint16_t* pidx;             // [32W] narrow state: the wider state's index of each vertex
+  uint8_t* sins;              // [D] insertion index of each pick in sid
   uint8_t* rr;                // [32W] r values (Algorithm 5), capped at k
-  uint8_t* dense;             // [KMAX] frame uses the memo
-  uint8_t* fullins;           // [KMAX] frame's whole set already stored
+  uint8_t* dense;             // [D] frame uses the memo
+  uint8_t* fullins;           // [D] frame's whole set already stored
   uint32_t* crow;             // [32] rows of a candidate set re-indexed to 0..31 (count_compact)
-  __host__ __device__ static constexpr size_t bytes() { return warp_state_raw(W); }
-  __device__ void carve(uint8_t* base) {
+  uint8_t* cbase;             // this warp's narrow branch state (shared memory), or nullptr
+  __device__ void carve(uint8_t* base, int D) {
     uint8_t* p = base;
-    sum = (unsigned long long*)p; p += (size_t)KMAX * 8;
+    sum = (unsigned long long*)p; p += (size_t)D * 8;
     crow = (uint32_t*)p; p += 32 * 4;
     nbr = (uint32_t*)p; p += (size_t)32 * W * 4;
     rows = (uint32_t*)p; p += (size_t)32 * W * W * 4;
-    masks = (uint32_t*)p; p += (size_t)KMAX * W * 4;
-    cand = (uint32_t*)p; p += (size_t)KMAX * W * 4;
-    pos = (int32_t*)p; p += (size_t)KMAX * 4;
-    cur = (int32_t*)p; p += (size_t)KMAX * 4;
-    sid = (uint32_t*)p; p += (size_t)(KMAX + 1) * 4;
-    sins = p; p += KMAX;
+    masks = (uint32_t*)p; p += (size_t)D * W * 4;
+    cand = (uint32_t*)p; p += (size_t)D * W * 4;
+    pos = (int32_t*)p; p += (size_t)D * 4;
+    cur = (int32_t*)p; p += (size_t)D * 4;
+    sid = (uint32_t*)p; p += (size_t)(D + 1) * 4;
+    pidx = (uint16_t*)p; p += (size_t)32 * W * 2;
+    sins = p; p += D;
     rr = p; p += 32 * W;
-    dense = p; p += KMAX;
+    dense = p; p += D;
     fullins = p;
+    cbase = nullptr;
   }
 };
-
-template <int W>
-__host__ __device__ constexpr size_t warp_state_bytes() {
-  return warp_state_stride(W);
-}
 
 // ------------------------------------------------------------ bit helpers
 // Largest set bit of (S & M) at index <= from, or -1.
@@ -244,6 +258,16 @@ __device__ __forceinline__ int memo_store(const Memo& m, const uint32_t (&key)[W
   return 1;
 }
 
+// A new trie for the next root: every entry of an older epoch is stale.
+__device__ __forceinline__ void next_epoch(Memo& memo, uint32_t* epoch) {
+  if (++*epoch >= (1u << 25)) {
+    for (uint32_t i = lane_id(); i < memo.cap; i += 32) memo.tags[i] = 0u;
+    __syncwarp();
+    *epoch = 1;
+  }
+  memo.tagbase = *epoch << 7;
+}
+
 // Bits of c at index >= v.
 template <int W>
 __device__ __forceinline__ void suffix_of(const uint32_t (&c)[W], int v, uint32_t (&out)[W]) {
@@ -274,8 +298,8 @@ __device__ __forceinline__ int select_bit(const uint32_t (&c)[W], int j) {
 // vertices v of S that can start a 3-clique (r_v >= 3) and each counts the
 // edges of S ∩ row(v) on its own.
 template <int W>
-__device__ __forceinline__ uint32_t tri_partial(const uint32_t (&S)[W], const uint32_t* rows, const uint32_t* m3,
-                                               uint32_t& ops) {
+__device__ __forceinline__ uint32_t tri_partial_body(const uint32_t (&S)[W], const uint32_t* rows, const uint32_t* m3,
+                                                    uint32_t& ops) {
   const uint32_t lane = lane_id();
   uint32_t acc = 0;
 #pragma unroll
@@ -301,6 +325,21 @@ __device__ __forceinline__ uint32_t tri_partial(const uint32_t (&S)[W], const ui
     }
   }
   return acc;
+}
+
+// Widths of 8 words and more count triangles out of line (its unrolled
+// W x W body is large and is reached from several call sites).
+template <int W>
+__device__ __noinline__ uint32_t tri_partial_outlined(const uint32_t (&S)[W], const uint32_t* rows, const uint32_t* m3,
+                                                      uint32_t& ops) {
+  return tri_partial_body<W>(S, rows, m3, ops);
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t tri_partial(const uint32_t (&S)[W], const uint32_t* rows, const uint32_t* m3,
+                                               uint32_t& ops) {
+  if constexpr (W >= 8) return tri_partial_outlined<W>(S, rows, m3, ops);
+  else return tri_partial_body<W>(S, rows, m3, ops);
 }
 
 // Cliques of size need + 1 whose smallest vertex is the caller's, given its
@@ -347,6 +386,8 @@ struct Acc {
   uint32_t ops = 0;          // candidate words intersected since the last fold into ops64
   unsigned long long ops64 = 0;
   unsigned long long pruned = 0, words = 0, hits = 0, ins = 0, full = 0, frames = 0, heavy = 0, tasks = 0;
+  unsigned long long build_ns = 0, busy_ns = 0;  // warp time (lane 0's account) in builds, and in all
+  unsigned long long ins_mark = 0, ins_peak = 0; // trie entries of the current root: inserts since ins_mark
 };
 
 // Steps 1 and 2 for root u: bitmap rows, Algorithm 5, masks.  Returns false
@@ -835,38 +876,171 @@ __device__ unsigned long long dfs_memo(WarpState<W>& st, const EnumKArgs& a, con
   return result;
 }
 
-// Widths 16 and 32 call the searches out of line: inlined at every call site
-// their unrolled 16- and 32-word loops make the build several times slower,
-// and at those widths the call costs little next to the work of a frame.
+// The searches are compiled once per width, in that width's translation
+// unit (kc_enum_w*.cu, relocatable device code), and called out of line from
+// every kernel: a width-W kernel also runs the narrow searches of smaller
+// widths, and inlining them all would multiply the build time.  A call per
+// root or branch costs little next to the search behind it.
 template <int W, int MODE>
-__device__ __noinline__ void dfs_plain_outlined(WarpState<W>& st, const EnumKArgs& a, int base, Acc& acc) {
-  dfs_plain<W, MODE>(st, a, base, acc);
-}
-
+__device__ void dfs_plain_call(WarpState<W>& st, const EnumKArgs& a, int base, Acc& acc);
 template <int W>
-__device__ __noinline__ unsigned long long dfs_memo_outlined(WarpState<W>& st, const EnumKArgs& a, const Memo& memo,
-                                                             int base, Acc& acc) {
-  return dfs_memo<W>(st, a, memo, base, acc);
+__device__ unsigned long long dfs_memo_call(WarpState<W>& st, const EnumKArgs& a, const Memo& memo, int base,
+                                            Acc& acc);
+
+#define KC_DFS_DECL(W)                                                                                    \
+  template <>                                                                                             \
+  __device__ void dfs_plain_call<W, 0>(WarpState<W> & st, const EnumKArgs& a, int base, Acc& acc);       \
+  template <>                                                                                             \
+  __device__ void dfs_plain_call<W, 1>(WarpState<W> & st, const EnumKArgs& a, int base, Acc& acc);       \
+  template <>                                                                                             \
+  __device__ unsigned long long dfs_memo_call<W>(WarpState<W> & st, const EnumKArgs& a, const Memo& memo, \
+                                                 int base, Acc& acc);
+KC_DFS_DECL(1)
+KC_DFS_DECL(2)
+KC_DFS_DECL(4)
+KC_DFS_DECL(8)
+KC_DFS_DECL(16)
+KC_DFS_DECL(32)
+
+// The definitions, for the width's own translation unit.
+#define KC_DFS_DEF(W)                                                                                           \
+  template <>                                                                                                   \
+  __device__ __noinline__ void dfs_plain_call<W, 0>(WarpState<W> & st, const EnumKArgs& a, int base, Acc& acc) { \
+    dfs_plain<W, 0>(st, a, base, acc);                                                                          \
+  }                                                                                                             \
+  template <>                                                                                                   \
+  __device__ __noinline__ void dfs_plain_call<W, 1>(WarpState<W> & st, const EnumKArgs& a, int base, Acc& acc) { \
+    dfs_plain<W, 1>(st, a, base, acc);                                                                          \
+  }                                                                                                             \
+  template <>                                                                                                   \
+  __device__ __noinline__ unsigned long long dfs_memo_call<W>(WarpState<W> & st, const EnumKArgs& a,            \
+                                                              const Memo& memo, int base, Acc& acc) {           \
+    return dfs_memo<W>(st, a, memo, base, acc);                                                                 \
+  }
+
+// The narrow state of a branch whose candidate set c (m vertices, in the
+// root's width W) fits in W2 words: vertex j of the narrow state is the j-th
+// smallest member of c, row j holds its larger neighbours inside c (one
+// ballot per row and word: lane t answers whether row s_j of the wide matrix
+// holds member t), and it keeps its rank, its r value and the masks by r.
+template <int W, int W2>
+__device__ void build_compact(const WarpState<W>& st, WarpState<W2>& cs, const uint32_t (&c)[W], int m, uint32_t need,
+                              Acc& acc) {
+  const uint32_t lane = lane_id();
+  int base = 0;
+#pragma unroll
+  for (int w = 0; w < W; w++) {
+    const uint32_t x = c[w];
+    if ((x >> lane) & 1u) cs.pidx[base + __popc(x & lanemask_lt())] = (uint16_t)((w << 5) + lane);
+    base += __popc(x);
+  }
+  __syncwarp();
+  for (int j = lane; j < m; j += 32) {
+    const int sp = cs.pidx[j];
+    cs.nbr[j] = st.nbr[sp];
+    cs.rr[j] = st.rr[sp];
+  }
+  for (int i = lane; i < m * W2; i += 32) cs.rows[i] = 0u;
+  __syncwarp();
+#pragma unroll 1
+  for (int q = 0; q < W2; q++) {
+    const int t = (q << 5) + (int)lane;  // this lane's narrow column
+    const bool have = t < m;
+    const int sp = have ? cs.pidx[t] : 0;
+    const int sw = sp >> 5;
+    const uint32_t sb = 1u << (sp & 31);
+    const int iend = min(m, (q << 5) + 31);  // rows i < t of this word
+#pragma unroll 1
+    for (int i0 = 0; i0 < iend; i0 += 32) {
+      const int cnt = min(32, iend - i0);
+      uint32_t mine = 0;
+#pragma unroll 1
+      for (int ii = 0; ii < cnt; ii++) {
+        const int i = i0 + ii;
+        const int si = cs.pidx[i];
+        const bool bit = have && t > i && (st.rows[(size_t)si * W + sw] & sb);
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, bit);
+        if ((int)lane == ii) mine = b;
+      }
+      if ((int)lane < cnt) cs.rows[(size_t)(i0 + lane) * W2 + q] = mine;
+    }
+  }
+  for (uint32_t l = 1; l <= need; l++) {
+#pragma unroll
+    for (int q = 0; q < W2; q++) {
+      const int t = (q << 5) + (int)lane;
+      const uint32_t mk = __ballot_sync(0xFFFFFFFFu, t < m && cs.rr[t] >= l);
+      if (lane == 0) cs.masks[l * W2 + q] = mk;
+    }
+  }
+  if (lane == 0) acc.ops += (uint32_t)(m * W2);  // one word produced per row and narrow word
+  __syncwarp();
+}
+
+// A branch searched in its narrow state: the frame at depth 1 holds every
+// narrow vertex; the clique prefix (root and v1) comes from the wide state.
+template <int W, int W2, int MODE>
+__device__ void run_narrow(WarpState<W>& st, const EnumKArgs& a, Memo& memo2, uint32_t* epoch2,
+                           const uint32_t (&c)[W], int m, Acc& acc) {
+  const uint32_t lane = lane_id();
+  WarpState<W2> cs;
+  cs.carve(st.cbase, (int)a.depth);
+  build_compact<W, W2>(st, cs, c, m, a.k - 1, acc);
+  uint32_t S[W2];
+  all_bits<W2>(m, S);
+  if (lane < W2) cs.cand[W2 + lane] = word_at<W2>(S, lane);
+  if (lane == 0) {
+    cs.pos[1] = m - 1;
+    if (MODE == 1) {
+      cs.sid[0] = st.sid[0];
+      cs.sid[1] = st.sid[1];
+    }
+    cs.sum[1] = 0;
+    cs.dense[1] = 0;
+    cs.fullins[1] = 0;
+  }
+  __syncwarp();
+  if (MODE == 2) {
+    next_epoch(memo2, epoch2);
+    const unsigned long long v = dfs_memo_call<W2>(cs, a, memo2, 1, acc);
+    if (lane == 0) acc.cnt += v;
+  } else {
+    dfs_plain_call<W2, MODE>(cs, a, 1, acc);
+  }
 }
 
 template <int W, int MODE>
-__device__ __forceinline__ void dfs_plain_at(WarpState<W>& st, const EnumKArgs& a, int base, Acc& acc) {
-  if constexpr (W >= 16) dfs_plain_outlined<W, MODE>(st, a, base, acc);
-  else dfs_plain<W, MODE>(st, a, base, acc);
+__device__ void narrow_dispatch(WarpState<W>& st, const EnumKArgs& a, Memo& memo2, uint32_t* epoch2,
+                                const uint32_t (&c)[W], int m, int W2, Acc& acc) {
+  if (W2 == 1) {
+    run_narrow<W, 1, MODE>(st, a, memo2, epoch2, c, m, acc);
+    return;
+  }
+  if constexpr (compact_width(W) >= 2) {
+    if (W2 == 2) {
+      run_narrow<W, 2, MODE>(st, a, memo2, epoch2, c, m, acc);
+      return;
+    }
+  }
+  if constexpr (compact_width(W) >= 4) {
+    if (W2 == 4) {
+      run_narrow<W, 4, MODE>(st, a, memo2, epoch2, c, m, acc);
+      return;
+    }
+  }
+  if constexpr (compact_width(W) >= 8) {
+    if (W2 == 8) run_narrow<W, 8, MODE>(st, a, memo2, epoch2, c, m, acc);
+  }
 }
 
-template <int W>
-__device__ __forceinline__ unsigned long long dfs_memo_at(WarpState<W>& st, const EnumKArgs& a, const Memo& memo,
-                                                          int base, Acc& acc) {
-  if constexpr (W >= 16) return dfs_memo_outlined<W>(st, a, memo, base, acc);
-  else return dfs_memo<W>(st, a, memo, base, acc);
-}
-
-// Everything below one first-level branch v1 of a built root (a task of the
-// split path, or a branch kept local): the (k-2)-cliques of G_u ∩ N(v1).
+// Everything below one first-level branch v1 of a built root (a branch of
+// the root's own loop, or a task of the split path): the (k-2)-cliques of
+// G_u ∩ N(v1).  A branch that is not dense by Eq. (1) and whose candidate set
+// fits a bit-matrix at most half as wide is searched in that narrow state.
 template <int W, int MODE>
-__device__ void run_branch(WarpState<W>& st, const EnumKArgs& a, const Memo& memo, uint32_t u, int d, int v1,
-                           Acc& acc, bool parent_dense) {
+__device__ __noinline__ void run_branch(WarpState<W>& st, const EnumKArgs& a, const Memo& memo, Memo& memo2,
+                                        uint32_t* epoch2,
+                           uint32_t u, int d, int v1, Acc& acc, bool parent_dense) {
   const uint32_t lane = lane_id();
   const uint32_t need = a.k - 1;
   uint32_t S0[W], c[W];
@@ -896,6 +1070,22 @@ __device__ void run_branch(WarpState<W>& st, const EnumKArgs& a, const Memo& mem
     acc.cnt += count_compact<W>(st, c, sz, cl, acc.ops);
     return;
   }
+  if (MODE == 1 && lane == 0) {
+    uint32_t iu = a.vert[u], iv = a.vert[st.nbr[v1]];
+    st.sid[0] = min(iu, iv);
+    st.sid[1] = max(iu, iv);
+  }
+  if constexpr (compact_width(W) > 0) {
+    if (!cd && (MODE == 1 ? cl >= 2 : cl >= 3)) {
+      const int W2 = sz <= 32 ? 1 : (sz <= 64 ? 2 : (sz <= 128 ? 4 : 8));
+      if (2 * W2 <= W && W2 <= compact_width(W)) {
+        __syncwarp();
+        if (MODE == 2 && memo2.cap == 0) narrow_dispatch<W, 0>(st, a, memo2, epoch2, c, (int)sz, W2, acc);
+        else narrow_dispatch<W, MODE>(st, a, memo2, epoch2, c, (int)sz, W2, acc);
+        return;
+      }
+    }
+  }
   if (MODE != 1 && cl <= 3) {
     unsigned long long v = small_count<W>(st, c, cl, acc);
     if (lane == 0) acc.cnt += v;
@@ -903,20 +1093,15 @@ __device__ void run_branch(WarpState<W>& st, const EnumKArgs& a, const Memo& mem
   }
   if (lane < W) st.cand[W + lane] = word_at<W>(c, lane);
   if (MODE == 1) {
-    if (lane == 0) {
-      uint32_t iu = a.vert[u], iv = a.vert[st.nbr[v1]];
-      st.sid[0] = min(iu, iv);
-      st.sid[1] = max(iu, iv);
-      st.pos[1] = top_bit<W>(c);
-    }
+    if (lane == 0) st.pos[1] = top_bit<W>(c);
     __syncwarp();
-    dfs_plain_at<W, 1>(st, a, 1, acc);
+    dfs_plain_call<W, 1>(st, a, 1, acc);
     return;
   }
   if (MODE == 0) {
     if (lane == 0) st.pos[1] = top_bit<W>(c);
     __syncwarp();
-    dfs_plain_at<W, 0>(st, a, 1, acc);
+    dfs_plain_call<W, 0>(st, a, 1, acc);
     return;
   }
   // MODE 2
@@ -933,7 +1118,7 @@ __device__ void run_branch(WarpState<W>& st, const EnumKArgs& a, const Memo& mem
     st.fullins[1] = 0;
   }
   __syncwarp();
-  unsigned long long v = dfs_memo_at<W>(st, a, memo, 1, acc);
+  unsigned long long v = dfs_memo_call<W>(st, a, memo, 1, acc);
   if (lane == 0) acc.cnt += v;
 }
 
@@ -991,7 +1176,8 @@ __device__ bool publish_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, i
   acc.tasks += nt;
   // branches past the queue's capacity stay with this warp
   if (t0 + nt > a.task_cap) {
-    Memo none{};
+    Memo none{}, none2{};
+    uint32_t ep2 = 0;
     uint32_t skip = t0 < a.task_cap ? (uint32_t)(a.task_cap - t0) : 0u;
     uint32_t idx = 0;
     for (int w = 0; w < W; w++) {
@@ -999,7 +1185,7 @@ __device__ bool publish_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, i
       while (x) {
         int b = __ffs(x) - 1;
         x &= x - 1;
-        if (idx++ >= skip) run_branch<W, MODE == 1 ? 1 : 0>(st, a, none, u, d, (w << 5) + b, acc, false);
+        if (idx++ >= skip) run_branch<W, MODE == 1 ? 1 : 0>(st, a, none, none2, &ep2, u, d, (w << 5) + b, acc, false);
       }
     }
   }
@@ -1025,51 +1211,67 @@ __device__ void flush_acc(const EnumKArgs& a, Acc& acc) {
     if (acc.frames) atomicAdd(&a.acc[kAccMemoFrames], acc.frames);
     if (acc.heavy) atomicAdd(&a.acc[kAccRootsHeavy], acc.heavy);
     if (acc.tasks) atomicAdd(&a.acc[kAccTasks], acc.tasks);
+    if (acc.build_ns) atomicAdd(&a.acc[kAccBuildNs], acc.build_ns);
+    if (acc.busy_ns) atomicAdd(&a.acc[kAccBusyNs], acc.busy_ns);
+    const unsigned long long peak = max(acc.ins_peak, acc.ins - acc.ins_mark);
+    if (peak) atomicMax(&a.acc[kAccMemoPeak], peak);
   }
 }
 
 template <int W>
 __device__ __forceinline__ void carve_state(WarpState<W>& st, const EnumKArgs& a, uint8_t* smem) {
   const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (a.gstate) st.carve(a.gstate + gwarp * a.gstride);
-  else st.carve(smem + (size_t)(threadIdx.x >> 5) * warp_state_bytes<W>());
+  uint8_t* mine = smem + (size_t)(threadIdx.x >> 5) * a.sstride;
+  if (a.gstate) st.carve(a.gstate + gwarp * a.gstride, (int)a.depth);
+  else st.carve(mine, (int)a.depth);
+  if (compact_width(W)) st.cbase = mine + a.coff;
 }
 
+// This warp's memo tables.  With a narrow branch state the table is halved:
+// the first half serves the root's index space, the second the narrow
+// subproblems (each of which starts its own epoch there).
 template <int W>
-__device__ __forceinline__ Memo warp_memo(const EnumKArgs& a) {
+__device__ __forceinline__ void warp_memo(const EnumKArgs& a, Memo* m, Memo* m2) {
   const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  Memo m{};
-  if (a.memo_cap) {
-    m.tags = a.memo_tags + gwarp * a.memo_cap;
-    m.keys = a.memo_keys + gwarp * a.memo_cap * W;
-    m.vals = a.memo_vals + gwarp * a.memo_cap;
-    m.cap = a.memo_cap;
+  *m = Memo{};
+  *m2 = Memo{};
+  if (!a.memo_cap) return;
+  m->tags = a.memo_tags + gwarp * a.memo_cap;
+  m->keys = a.memo_keys + gwarp * a.memo_cap * W;
+  m->vals = a.memo_vals + gwarp * a.memo_cap;
+  m->cap = a.memo_cap;
+  if (compact_width(W) && a.memo_cap >= 64) {
+    const uint32_t h = a.memo_cap / 2;
+    m->cap = h;
+    m2->tags = m->tags + h;
+    m2->keys = m->keys + (size_t)h * W;  // the narrow keys (width <= W/2) fit in the same stride
+    m2->vals = m->vals + h;
+    m2->cap = h;
   }
-  return m;
 }
 
-__device__ __forceinline__ void next_epoch(Memo& memo, uint32_t* epoch) {
-  if (++*epoch >= (1u << 25)) {
-    for (uint32_t i = lane_id(); i < memo.cap; i += 32) memo.tags[i] = 0u;
-    __syncwarp();
-    *epoch = 1;
-  }
-  memo.tagbase = *epoch << 7;
-}
 
 // Phase 1: one warp per root, roots taken from the tier's list.
 // MODE 0: count (plain), 1: list, 2: count with memo.
 // Everything for one root u of the graph in `a`: build, prune, then split,
 // count or list.  Counts accumulate in acc.cnt (lane-partial).
 template <int W, int MODE>
-__device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint32_t* epoch, uint32_t u, Acc& acc) {
+__device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint32_t* epoch, Memo& memo2,
+                          uint32_t* epoch2, uint32_t u, Acc& acc) {
   const uint32_t lane = lane_id();
   const uint32_t need = a.k - 1;
   const int d = (int)(a.orow[u + 1] - a.orow[u]);
-  if (!build_root<W>(st, a, u, d, acc)) return;
+  const unsigned long long tb = global_ns();
+  const bool kept = build_root<W>(st, a, u, d, acc);
+  if (lane == 0) acc.build_ns += global_ns() - tb;
+  if (!kept) return;
   uint32_t S0[W];
   all_bits<W>(d, S0);
-  if (MODE == 2) next_epoch(memo, epoch);
+  if (MODE == 2) {
+    next_epoch(memo, epoch);
+    acc.ins_peak = max(acc.ins_peak, acc.ins - acc.ins_mark);
+    acc.ins_mark = acc.ins;
+  }
   // Eq. (1) on G_u for the root frame
   bool dense0 = false;
   if (MODE == 2 && a.memo && need > 3) {
@@ -1096,7 +1298,17 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
     const uint32_t thr = dense0 ? (a.split_wedges >> min(need - 4u, 12u)) : a.split_wedges;
     if (wg > thr && publish_root<W, MODE>(st, a, u, d, acc, d, dense0)) return;
   }
-  if (MODE != 1 && need >= 2 && need <= kCompactMaxL && d <= 32 && !dense0) {
+  if (W >= 2 && (need >= 4 || (MODE == 1 && need >= 2))) {
+    // the root frame of a wide root: one branch after another, from the
+    // largest vertex down (the order of the identifying strings, so that a
+    // dense branch resumes from its sibling's stored set), each searched in
+    // a narrow state where its candidate set allows
+    if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
+    __syncwarp();
+    const uint32_t* m1 = st.masks + need * W;
+    for (int v1 = next_desc<W>(st.cand, m1, d - 1); v1 >= 0; v1 = next_desc<W>(st.cand, m1, v1 - 1))
+      run_branch<W, MODE>(st, a, memo, memo2, epoch2, u, d, v1, acc, dense0);
+  } else if (MODE != 1 && need >= 2 && need <= kCompactMaxL && d <= 32 && !dense0) {
     // the whole root at once: one word per row, lanes take the smallest vertex
     acc.cnt += count_compact<W>(st, S0, (uint32_t)d, need, acc.ops);
   } else if (MODE == 0 || MODE == 1) {
@@ -1106,7 +1318,7 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
       if (MODE == 1) st.sid[0] = a.vert[u];
     }
     __syncwarp();
-    dfs_plain_at<W, MODE>(st, a, 0, acc);
+    dfs_plain_call<W, MODE>(st, a, 0, acc);
   } else {
     if (need <= 3) {
       unsigned long long v = small_count<W>(st, S0, need, acc);
@@ -1120,7 +1332,7 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
         st.fullins[0] = 0;
       }
       __syncwarp();
-      unsigned long long v = dfs_memo_at<W>(st, a, memo, 0, acc);
+      unsigned long long v = dfs_memo_call<W>(st, a, memo, 0, acc);
       if (lane == 0) acc.cnt += v;
     }
   }
@@ -1160,23 +1372,26 @@ __global__ void __launch_bounds__(256) k_enum(const __grid_constant__ EnumKArgs 
   WarpState<W> st;
   carve_state<W>(st, a, smem);
   Acc acc;
-  Memo memo = warp_memo<W>(a);
-  uint32_t epoch = 0;
+  Memo memo, memo2;
+  warp_memo<W>(a, &memo, &memo2);
+  uint32_t epoch = 0, epoch2 = 0;
   while (true) {
     uint32_t qi = 0;
     if (lane == 0) qi = atomicAdd(a.qctr, 1u);
     qi = __shfl_sync(0xFFFFFFFFu, qi, 0);
     if (qi >= a.nroots) break;
     const uint32_t u = a.roots[qi];
+    const unsigned long long t0 = global_ns();
     if (a.bq) {
       const uint32_t q = a.roots_q[qi];
       EnumKArgs b = a;
       bind_query(b, a, q);
-      root_body<W, MODE>(st, b, memo, &epoch, u, acc);
+      root_body<W, MODE>(st, b, memo, &epoch, memo2, &epoch2, u, acc);
       flush_query<MODE>(a, q, acc);
     } else {
-      root_body<W, MODE>(st, a, memo, &epoch, u, acc);
+      root_body<W, MODE>(st, a, memo, &epoch, memo2, &epoch2, u, acc);
     }
+    if (lane == 0) acc.busy_ns += global_ns() - t0;
     acc.ops64 += acc.ops;
     acc.ops = 0;
     __syncwarp();
@@ -1195,8 +1410,9 @@ __global__ void __launch_bounds__(256) k_tasks(const __grid_constant__ EnumKArgs
   EnumKArgs b = a;  // bound to the current root's query in a batch
   uint32_t need = a.k - 1;
   Acc acc;
-  Memo memo = warp_memo<W>(a);
-  uint32_t epoch = 1u << 24;  // above every epoch of phase 1
+  Memo memo, memo2;
+  warp_memo<W>(a, &memo, &memo2);
+  uint32_t epoch = 1u << 24, epoch2 = 1u << 24;  // above every epoch of phase 1
   const unsigned long long ntasks = min(*(volatile unsigned long long*)a.task_used, a.task_cap);
   unsigned long long cur = ~0ull;
   uint32_t u = 0;
@@ -1207,6 +1423,7 @@ __global__ void __launch_bounds__(256) k_tasks(const __grid_constant__ EnumKArgs
     if (lane == 0) t = atomicAdd(a.task_head, 1ull);
     t = __shfl_sync(0xFFFFFFFFu, t, 0);
     if (t >= ntasks) break;
+    const unsigned long long t0 = global_ns();
     const unsigned long long task = a.tasks[t];
     const unsigned long long off = task >> 32;
     const int v1 = (int)(task & 0xFFFFFFFFull);
@@ -1240,11 +1457,16 @@ __global__ void __launch_bounds__(256) k_tasks(const __grid_constant__ EnumKArgs
       }
       __syncwarp();
       cur = off;
-      if (MODE == 2) next_epoch(memo, &epoch);
+      if (MODE == 2) {
+        next_epoch(memo, &epoch);
+        acc.ins_peak = max(acc.ins_peak, acc.ins - acc.ins_mark);
+        acc.ins_mark = acc.ins;
+      }
     }
     // the kernel's own arguments are read in place; only a batch binds a copy
-    run_branch<W, MODE>(st, a.bq ? b : a, memo, u, d, v1, acc, dense);
+    run_branch<W, MODE>(st, a.bq ? b : a, memo, memo2, &epoch2, u, d, v1, acc, dense);
     if (a.bq) flush_query<MODE>(a, b.query, acc);
+    if (lane == 0) acc.busy_ns += global_ns() - t0;
     acc.ops64 += acc.ops;
     acc.ops = 0;
     __syncwarp();

@@ -3,5 +3,6 @@
 #include "kc_enum_dev.cuh"
 
 namespace kc {
+KC_DFS_DEF(16)
 KC_TIER_KERNELS(16, 1)
 }  // namespace kc

@@ -164,6 +164,9 @@ enum AccSlot : int {
   kAccMemoFrames,
   kAccTasks,
   kAccWordOps,
+  kAccBuildNs,     // warp-nanoseconds spent building root bit-matrices (a5)
+  kAccBusyNs,      // warp-nanoseconds spent on roots and tasks in all
+  kAccMemoPeak,    // most trie entries stored for one root
   kAccQueue0,      // root-queue counters (one per width tier)
   kAccArena0 = kAccQueue0 + kTiers,     // split path: arena units used, per tier
   kAccTaskUsed0 = kAccArena0 + kTiers,  // split path: tasks queued, per tier

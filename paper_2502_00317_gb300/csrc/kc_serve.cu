@@ -100,7 +100,9 @@ uint64_t request_bytes(uint32_t n, uint64_t nnz, bool inline_csr, const uint32_t
     const uint64_t unit = ((16 + 128 * W + 128 * W * W + 32 * W + 15) / 16) * 16;  // one published root
     b += roots * (unit + 8 * 32 * W);                                            // and its tasks
   }
-  if (inline_csr) b += 48ull * n + 8ull * nnz + 64;
+  // upload of an inline graph: input copy, canonicalisation, peel and sort
+  // work arrays, and the graph's own order and DAG arrays
+  if (inline_csr) b += 96ull * n + 24ull * nnz + 1024;
   return b;
 }
 
@@ -168,14 +170,13 @@ void lane_loop(Server* S, int li) {
         }
         if (S->reserved + r.bytes > rcap) break;
         S->reserved += r.bytes;
-        S->peak_reserved = std::max(S->peak_reserved, S->reserved + lanes_scratch(S));
+        S->peak_reserved = std::max(S->peak_reserved, S->reserved + S->lane_budget * S->lanes.size());
         batch.push_back(std::move(r));
         S->queue.pop_front();
       }
     }
     if (batch.empty()) continue;
     const uint64_t t_start = now_ns();
-    lane->scratch_peak = lane->scratch_bytes;
     // inline graphs: upload on this lane
     std::vector<kc_graph> uploaded(batch.size(), 0);
     std::vector<const DevGraph*> graph(batch.size(), nullptr);
@@ -243,12 +244,9 @@ void lane_loop(Server* S, int li) {
     for (size_t i = 0; i < batch.size(); i++)
       if (uploaded[i]) kc_free_graph(lane, uploaded[i]);
     const uint64_t t_done = now_ns();
-    const uint64_t peak_here = lane->scratch_peak;
     if (lane->scratch_bytes > S->lane_budget) release_scratch(lane);
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      // this batch's high-water mark beside what the others hold
-      S->peak_reserved = std::max(S->peak_reserved, S->reserved + lanes_scratch(S) - S->lane_scratch[li] + peak_here);
       for (size_t i = 0; i < batch.size(); i++) {
         const ServeReq& r = batch[i];
         int rs = r.status;

@@ -97,6 +97,9 @@ class kc_stats(ctypes.Structure):
         ("ms_tier", ctypes.c_float * 6),
         ("roots_tier", ctypes.c_uint32 * 6),
         ("word_ops", ctypes.c_uint64),
+        ("warp_ns_build", ctypes.c_uint64),
+        ("warp_ns_busy", ctypes.c_uint64),
+        ("memo_peak", ctypes.c_uint64),
     ]
 
 

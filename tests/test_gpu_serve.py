@@ -109,40 +109,52 @@ def test_inline_graphs_and_admission_cap():
                 low[0] = min(low[0], torch.cuda.mem_get_info()[0])
                 stop.wait(0.002)
 
-        w = th.Thread(target=watch)
+        w = th.Thread(target=watch, daemon=True)
         w.start()
-        kc.kc_serve_start(c.h, lanes=2, max_batch=16, mem_cap_bytes=cap)
-        jobs = []
-        for i, g in enumerate(graphs):
-            for k in (3, 5, 7):
-                for mode in (kc.KC_SERVE_COUNT, kc.KC_SERVE_LIST):
-                    jobs.append((kc.kc_serve_submit_csr(c.h, g.n, g.rowptr, g.col, k, mode=mode), g, k, mode))
-                    jobs.append((kc.kc_serve_submit(c.h, hs[i], k, mode), g, k, mode))
-        # a raw CSR that the lane must canonicalise
-        jobs.append((kc.kc_serve_submit_csr(c.h, raw.n, raw.rowptr, raw.col, 4, canonicalize=True), raw, 4, 0))
-        jobs.append((kc.kc_serve_submit_csr(c.h, raw.n, raw.rowptr, raw.col, 4, canonicalize=True,
-                                            mode=kc.KC_SERVE_LIST), raw, 4, 1))
-        t_huge = kc.kc_serve_submit_csr(c.h, huge.n, huge.rowptr, huge.col, 3)
-        oracles = {}
-        for t, g, k, mode in jobs:
-            r = kc.kc_serve_wait(c.h, t, 120000)
-            assert r["status"] == kc.KC_OK
-            og = oracles.setdefault(id(g), oracle.OracleGraph.from_graph(g))
-            want = og.checksum(k)
-            assert r["count"] == want[0], (g.name, k)
-            assert r["checksum"] == (want[1] if mode == kc.KC_SERVE_LIST else 0), (g.name, k)
-        r = kc.kc_serve_wait(c.h, t_huge, 120000)
-        assert r["status"] == kc.KC_E_OOM
-        st = kc.kc_serve_stats_get(c.h)
-        kc.kc_serve_stop(c.h)
-        stop.set()
-        w.join()
-        assert 0 < st["peak_reserved_bytes"] <= cap
+        try:
+            _serve_inline(c, graphs, hs, huge, raw, cap)
+        finally:
+            stop.set()
+            w.join()
+            if kc.kc_serve_stats_get(c.h)["submitted"]:
+                try:
+                    kc.kc_serve_stop(c.h)
+                except kc.KcError:
+                    pass
         # what the device really lost while serving: the cap, plus the lanes' fixed
         # records (streams, events, accumulators) and the allocator's rounding
         assert free0 - low[0] <= cap + (32 << 20), (free0 - low[0], cap)
         for h in hs:
             c.free(h)
+
+
+def _serve_inline(c, graphs, hs, huge, raw, cap):
+    """Inline and resident requests, counted and listed, under a 256 MiB cap."""
+    kc.kc_serve_start(c.h, lanes=2, max_batch=16, mem_cap_bytes=cap)
+    jobs = []
+    for i, g in enumerate(graphs):
+        for k in (3, 5, 7):
+            for mode in (kc.KC_SERVE_COUNT, kc.KC_SERVE_LIST):
+                jobs.append((kc.kc_serve_submit_csr(c.h, g.n, g.rowptr, g.col, k, mode=mode), g, k, mode))
+                jobs.append((kc.kc_serve_submit(c.h, hs[i], k, mode), g, k, mode))
+    # a raw CSR that the lane must canonicalise
+    jobs.append((kc.kc_serve_submit_csr(c.h, raw.n, raw.rowptr, raw.col, 4, canonicalize=True), raw, 4, 0))
+    jobs.append((kc.kc_serve_submit_csr(c.h, raw.n, raw.rowptr, raw.col, 4, canonicalize=True,
+                                        mode=kc.KC_SERVE_LIST), raw, 4, 1))
+    t_huge = kc.kc_serve_submit_csr(c.h, huge.n, huge.rowptr, huge.col, 3)
+    oracles = {}
+    for t, g, k, mode in jobs:
+        r = kc.kc_serve_wait(c.h, t, 120000)
+        assert r is not None and r["status"] == kc.KC_OK, (g.name, k, mode, r)
+        og = oracles.setdefault(id(g), oracle.OracleGraph.from_graph(g))
+        want = og.checksum(k)
+        assert r["count"] == want[0], (g.name, k)
+        assert r["checksum"] == (want[1] if mode == kc.KC_SERVE_LIST else 0), (g.name, k)
+    r = kc.kc_serve_wait(c.h, t_huge, 120000)
+    assert r["status"] == kc.KC_E_OOM
+    st = kc.kc_serve_stats_get(c.h)
+    kc.kc_serve_stop(c.h)
+    assert 0 < st["peak_reserved_bytes"] <= cap, (st, cap)
 
 
 def test_stop_ends_every_request_and_errors():

@@ -44,9 +44,12 @@ def _args():
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--ks", type=str, default=",".join(map(str, KS)))
     p.add_argument("--small", action="store_true", help="a small graph (for profiling runs)")
-    p.add_argument("--workload", choices=("sweep", "batched", "serve"), default="sweep",
+    p.add_argument("--workload", choices=("sweep", "batched", "serve", "rmat", "ablation"), default="sweep",
                    help="sweep: config 2 k=5..9 (default); batched: config 4, 4,096 graphs in one kc_count_batched; "
-                        "serve: config 5, Poisson arrivals served by kc_serve_*")
+                        "serve: config 5, Poisson arrivals served by kc_serve_*; rmat: config 3, R-MAT scale 22 k=6 "
+                        "listing of a root-range chunk into a device buffer; ablation: memo / pruning / split / "
+                        "decomposition variants on configs 2 and 3")
+    p.add_argument("--chunk", type=float, default=2 ** 29, help="rmat: about this many cliques in the listed chunk")
     p.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
     p.add_argument("--duration", type=float, default=20.0, help="serve: seconds of arrivals")
     p.add_argument("--count", type=int, default=4096, help="graphs in the batched workload")
@@ -611,6 +614,134 @@ def run_serve(a):
     ctx.close()
 
 
+def run_rmat(a):
+    """Config 3: R-MAT scale 22, k = 6.  The full listing holds 3.3e14 cliques
+    (8 PB of tuples), so the timed step lists one root-range chunk of the
+    dense core -- starting at the first rank whose out-degree reaches 512 and
+    widened until it holds about --chunk cliques -- into a device buffer with
+    its total and checksum (kc_list_range).  Also reported: one full k = 6
+    count and the upload, each timed once."""
+    from paper_2502_00317_gb300 import graphgen as gg
+
+    g = gg.config_rmat()
+    import torch
+
+    from paper_2502_00317_gb300 import kclique as kc
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = kc.Context(local)
+    k = 6
+    t0 = time.time()
+    h = ctx.upload_host(g.n, g.rowptr, g.col, canonicalize=True)
+    upload_s = time.time() - t0
+    up = ctx.upload_stats()
+    info = ctx.info(h)
+    _, _, orow, _ = ctx.export_dag(h)
+    d = np.diff(orow.astype(np.int64))
+    lo = int(np.argmax(d >= 512)) if (d >= 512).any() else int(np.argmax(d))
+    w, total = 64, 0
+    while True:
+        hi = min(info["n"], lo + w)
+        _, total, _ = ctx.list_range(h, k, lo, hi, None, 0, stream)
+        if total >= a.chunk or hi == info["n"]:
+            break
+        w *= 2
+    buf = torch.empty(max(total * k, 1), dtype=torch.int32, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    for _ in range(a.warmup):
+        ref = ctx.list_range(h, k, lo, hi, buf, total, stream)
+    times = []
+    sampler = ClockSampler(local)
+    sampler.start()
+    for _ in range(a.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        got = ctx.list_range(h, k, lo, hi, buf, total, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert got == ref, "listing changed between steps"
+        times.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    st = ctx.stats()
+    ms = statistics.mean(times)
+    hbm = _peaks().get("hbm_gbs")
+    write_gbs = 4 * k * total / (ms / 1e3) / 1e9
+    torch.cuda.synchronize()
+    t1 = time.time()
+    full = ctx.count(h, k, stream)
+    count_s = time.time() - t1
+    cst = ctx.stats()
+    line = {
+        "metric": "k-cliques/s (k=6 listing with checksum into a device buffer, root-range chunk)",
+        "value": total / (ms / 1e3), "unit": "k-cliques/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32/u64 (exact integer)", "data": "synthetic (seeded generator)",
+        "config": {"workload": "rmat_scale22_ef16_abcd.57.19.19.05_seed2_k6", "ranks": [lo, hi],
+                   "chunk_cliques": total, "checksum": ref[2], "buffer_bytes": 4 * k * total,
+                   "l2": "flushed between timed steps"},
+        "graph": info, "upload_s": upload_s, "upload_stage_ms": up,
+        "roofline": {"kernel": "listing family (k_enum + k_tasks, mode list with the trie)", "bound": "hbm",
+                     "achieved": round(write_gbs, 2), "peak": hbm, "unit": "GB/s (4k bytes of tuples per clique)",
+                     "frac": round(write_gbs / hbm, 4) if hbm else None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "list_stats": {kk: st[kk] for kk in ("ms_enum", "word_ops", "memo_hits", "memo_inserts", "memo_peak",
+                                             "roots_total", "roots_heavy")},
+        "full_count": {"k": k, "count": full, "seconds": count_s, "word_ops": cst["word_ops"],
+                       "memo_hits": cst["memo_hits"], "ms_tier": cst["ms_tier"], "roots_tier": cst["roots_tier"]},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_ablation(a):
+    """NEXT-3 (Sec. VII-C's baseline / memo / memo + pruning comparison, and
+    the decomposition of Sec. VII-D): each variant counts config 2 for
+    k = 5..9 (the memo-off variants up to k = 7) and config 3 for k = 5; per
+    count its enumeration time, candidate words intersected and the most trie
+    entries stored for one root."""
+    import torch
+
+    from paper_2502_00317_gb300 import graphgen as gg
+    from paper_2502_00317_gb300 import kclique as kc
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    variants = [("default", {}), ("no_prune", {"no_prune": True}), ("no_split", {"split_threshold": 0xFFFFFFFF}),
+                ("no_memo", {"no_memo": True}), ("baseline", {"no_memo": True, "no_prune": True}),
+                ("edge_parallel", {"decomposition": kc.KC_EDGE_PARALLEL}),
+                ("edge_parallel_no_memo", {"decomposition": kc.KC_EDGE_PARALLEL, "no_memo": True})]
+    out = {}
+    for gname, g, ks, canon in (("config2", gg.config_chung_lu(), KS, False),
+                                ("config3", gg.config_rmat(), (5,), True)):
+        rows = {}
+        for vname, opts in variants:
+            ctx = kc.Context(local, **opts)
+            h = ctx.upload_host(g.n, g.rowptr, g.col, canonicalize=canon)
+            per_k = {}
+            for k in ks:
+                if "no_memo" in opts and k > 7:
+                    continue
+                ctx.count(h, k)  # warm
+                c = ctx.count(h, k)
+                st = ctx.stats()
+                per_k[k] = {"count": c, "ms_enum": round(st["ms_enum"], 3), "word_ops": st["word_ops"],
+                            "memo_hits": st["memo_hits"], "memo_inserts": st["memo_inserts"],
+                            "memo_peak": st["memo_peak"], "roots_heavy": st["roots_heavy"]}
+            rows[vname] = per_k
+            ctx.close()
+        out[gname] = rows
+    if rank == 0:
+        print(json.dumps({"metric": "ablation: enumeration ms, word-ops, trie entries per root", "value": None,
+                          "unit": "ms", "n_gpus": ws, "data": "synthetic (seeded generator)",
+                          "config": {"workload": "ablation_config2_k5-9_config3_k5"}, "ablation": out}), flush=True)
+
+
 if __name__ == "__main__":
     args = _args()
     if args.impl == "reference":
@@ -619,5 +750,9 @@ if __name__ == "__main__":
         run_batched(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "rmat":
+        run_rmat(args)
+    elif args.workload == "ablation":
+        run_ablation(args)
     else:
         run_ours(args)

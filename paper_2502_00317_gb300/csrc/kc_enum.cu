@@ -72,6 +72,7 @@ struct TierPlan {
   uint32_t coff = 0;           // offset of the narrow branch state in them
   uint32_t memo_cap = 0;       // entries per warp (0: no memo)
   uint64_t memo_bytes = 0;
+  uint32_t larena_bytes = 0;   // listing with the memo: arena bytes per warp
   bool split = false;          // heavy roots of this tier go to the split path
   uint64_t arena_units = 0;    // 16-byte units for published roots
   uint64_t task_cap = 0;       // (root, branch) task slots
@@ -134,7 +135,7 @@ static int plan_tier(kc_ctx* ctx, int t, int mode, uint32_t nroots, bool split, 
     tp->gstate_bytes = wbytes;
   }
   tp->blocks = blocks;
-  if (mode == 2) {
+  if (mode == 2 || mode == 3) {
     // per-warp memo tables within the budget (the tau of Sec. VI), shared by the tiers;
     // a window of 32 slots is the smallest table, and a tier that cannot get one counts without
     uint64_t warps = blocks * tp->warps_per_block;
@@ -143,8 +144,8 @@ static int plan_tier(kc_ctx* ctx, int t, int mode, uint32_t nroots, bool split, 
     uint64_t per_entry = 4 + 4ull * W + 8;
     while (cap > 32 && warps * cap * per_entry > budget / kTiers) cap >>= 1;
     if (warps * cap * per_entry > budget / kTiers) {
-      tp->mode = 0;
-      tier_kernels(t, 0, &tp->fn, &tp->fn_tasks);
+      tp->mode = mode == 3 ? 1 : 0;
+      tier_kernels(t, tp->mode, &tp->fn, &tp->fn_tasks);
       if (tp->smem > 48 * 1024) {
         KC_CUDA(cudaFuncSetAttribute(tp->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp->smem));
         KC_CUDA(cudaFuncSetAttribute(tp->fn_tasks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp->smem));
@@ -152,6 +153,13 @@ static int plan_tier(kc_ctx* ctx, int t, int mode, uint32_t nroots, bool split, 
     } else {
       tp->memo_cap = cap;
       tp->memo_bytes = warps * cap * per_entry;
+      if (mode == 3) {
+        // the stored clique lists: up to four times the memo budget over the
+        // tiers, 4 KiB to 256 KiB per warp
+        const uint64_t per = std::min<uint64_t>(256 << 10, 4 * budget / kTiers / std::max<uint64_t>(warps, 1));
+        tp->larena_bytes = (uint32_t)(per & ~(uint64_t)15);
+        if (tp->larena_bytes < (4u << 10)) tp->larena_bytes = 0;  // too small to pay: plain listing tables only
+      }
     }
   }
   return KC_OK;
@@ -187,12 +195,14 @@ static int launch_tiers(kc_ctx* ctx, const EnumKArgs& args, const uint32_t* hcnt
   KC_TRY(plan_all(ctx, mode, hcnt, split, edge, args.depth, plans));
   // one scratch region for every tier's global state, memo tables, arena and task queue
   uint64_t total = 0;
-  uint64_t goff[kTiers], moff[kTiers], aoff[kTiers], toff[kTiers];
+  uint64_t goff[kTiers], moff[kTiers], loff[kTiers], aoff[kTiers], toff[kTiers];
   for (int t = 0; t < kTiers; t++) {
     goff[t] = total;
     total += (plans[t].gstate_bytes * plans[t].blocks * std::max(plans[t].warps_per_block, 1) + 255) & ~255ull;
     moff[t] = total;
     total += (plans[t].memo_bytes + 255) & ~255ull;
+    loff[t] = total;
+    total += ((uint64_t)plans[t].larena_bytes * plans[t].blocks * std::max(plans[t].warps_per_block, 1) + 255) & ~255ull;
     aoff[t] = total;
     total += (plans[t].arena_units * 16 + 255) & ~255ull;
     toff[t] = total;
@@ -225,6 +235,10 @@ static int launch_tiers(kc_ctx* ctx, const EnumKArgs& args, const uint32_t* hcnt
       x.memo_keys = (uint32_t*)(mb + warps * tp.memo_cap * 12);
       x.memo_cap = tp.memo_cap;
       KC_CUDA(cudaMemsetAsync(x.memo_tags, 0, warps * tp.memo_cap * 4, ts));
+    }
+    if (tp.larena_bytes) {
+      x.larena = (uint8_t*)base + loff[t];
+      x.larena_bytes = tp.larena_bytes;
     }
     if (tp.split) {
       x.split_wedges = split_ok ? split_wedges : 0u;
@@ -296,7 +310,8 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
     KC_CUDA(cudaEventRecord(ev[6], s));
     if (hcnt[kTiers] != 0) return KC_E_UNSUPPORTED;  // out-degree above the widest tier
     // memo needs at least one level to split (k >= 3); k = 2 counts by popcount
-    const int mode = ea.mode == 1 ? 1 : ((ea.memo && k >= 3) ? 2 : 0);
+    // listing uses the trie where Eq. (1) can hold below the first branch (k >= 6)
+    const int mode = ea.mode == 1 ? ((ea.memo && k >= 6) ? 3 : 1) : ((ea.memo && k >= 3) ? 2 : 0);
     EnumKArgs args{};
     args.orow = g.orow;
     args.ocol = g.ocol;

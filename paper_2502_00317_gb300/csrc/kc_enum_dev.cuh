@@ -29,6 +29,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "kc_internal.cuh"
 
@@ -55,6 +56,8 @@ struct EnumKArgs {
   uint32_t* memo_keys;
   unsigned long long* memo_vals;
   uint32_t memo_cap;          // entries per warp (power of two)
+  uint8_t* larena;            // listing with the trie: per-warp arenas of stored l-clique lists
+  uint32_t larena_bytes;      // bytes per warp
   uint32_t* status;
   // split path (heavy roots): arena of published roots and a task queue
   uint32_t split_wedges;      // 0: never split
@@ -82,7 +85,7 @@ struct EnumKArgs {
 // Bytes of one warp's working state at width W with stacks of depth D (the
 // layout of WarpState::carve; D = k + 1 covers every depth of a k-clique search).
 __host__ __device__ constexpr size_t warp_state_raw(int W, int D) {
-  return (size_t)D * 8 + 32 * 4 + (size_t)32 * W * 4 + (size_t)32 * W * W * 4 + (size_t)D * W * 4 * 2 +
+  return (size_t)D * 8 + 32 * 4 + (size_t)32 * W * 4 * 2 + (size_t)32 * W * W * 4 + (size_t)D * W * 4 * 2 +
          (size_t)D * 4 * 2 + (size_t)(D + 1) * 4 + (size_t)32 * W * 2 + D + 32 * W + D + D;
 }
 
@@ -104,6 +107,7 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int W, int D) {
 template <int W>
 struct WarpState {
   uint32_t* nbr;              // [32W] ranks of N+(u), ascending
+  uint32_t* oid;              // [32W] original ids of those vertices (listing with the trie)
   uint32_t* rows;             // [32W*W] bit-matrix rows
   uint32_t* masks;            // [D*W] masks[l*W+w]: local vertices with r >= l
   uint32_t* cand;             // [D*W] candidate set per depth
@@ -123,6 +127,7 @@ struct WarpState {
     sum = (unsigned long long*)p; p += (size_t)D * 8;
     crow = (uint32_t*)p; p += 32 * 4;
     nbr = (uint32_t*)p; p += (size_t)32 * W * 4;
+    oid = (uint32_t*)p; p += (size_t)32 * W * 4;
     rows = (uint32_t*)p; p += (size_t)32 * W * W * 4;
     masks = (uint32_t*)p; p += (size_t)D * W * 4;
     cand = (uint32_t*)p; p += (size_t)D * W * 4;
@@ -194,7 +199,15 @@ struct Memo {
   unsigned long long* vals;
   uint32_t cap;
   uint32_t tagbase;  // epoch << 7
+  uint8_t* lar;      // listing with the trie: this warp's arena of stored clique lists
+  uint32_t lcap;     // its bytes
+  uint32_t* ltop;    // bytes the current root has used (lives in the kernel)
 };
+
+// MODE 1 lists plainly, MODE 3 lists with the trie (both report cliques).
+__host__ __device__ constexpr bool is_list(int mode) { return mode == 1 || mode == 3; }
+// MODE 2 counts with the trie, MODE 3 lists with it.
+__host__ __device__ constexpr bool uses_trie(int mode) { return mode == 2 || mode == 3; }
 
 template <int W>
 __device__ __forceinline__ uint32_t memo_hash(const uint32_t (&key)[W], uint32_t l) {
@@ -876,6 +889,270 @@ __device__ unsigned long long dfs_memo(WarpState<W>& st, const EnumKArgs& a, con
   return result;
 }
 
+// ----------------------------------------------- listing with the trie
+// MODE 3 lists like MODE 1 and reuses repeated sub-searches the way the
+// Induced Subgraph Trie does for listing (Sec. IV, Algorithms 3 and 4): in a
+// dense region (Eq. (1); below a dense frame every frame, as Algorithm 3
+// recurses into itself) the l-cliques of a frame's set S are stored once --
+// as tuples of local indices in this warp's arena, keyed by (S, l) in the
+// warp's hash table -- and a later frame with the same (S, l) under another
+// clique prefix replays them (ListingIST) instead of searching: each stored
+// tuple joined with the prefix is emitted, lanes taking one tuple each.  A
+// frame is recorded only while no ancestor is recording and when its C(|S|,
+// l) upper bound fits the arena; the arena and table start empty for every
+// root.  Replays and searches emit exactly the same cliques.
+
+// C(m, l) saturated at 2^32 - 1: an upper bound on the l-cliques of an m-set.
+__device__ __forceinline__ uint32_t binom_sat(uint32_t m, uint32_t l) {
+  if (l > m) return 0;
+  unsigned long long c = 1;
+  for (uint32_t i = 1; i <= l; i++) {
+    c = c * (m - l + i) / i;  // C(m - l + i, i), exact at every step
+    if (c > 0xFFFFFFFFull) return 0xFFFFFFFFu;
+  }
+  return (uint32_t)c;
+}
+
+// Local-index type of stored tuples: one byte while a root has at most 256
+// out-neighbours (widths up to 8 words), two beyond.
+template <int W>
+using LIdx = typename std::conditional<(W <= 8), uint8_t, uint16_t>::type;
+
+// Emits prefix ∪ t for every stored tuple t (cnt tuples of lt local indices):
+// ids sorted, hashed, written, one tuple per lane.
+template <int W>
+__device__ void list_replay(const WarpState<W>& st, const EnumKArgs& a, const LIdx<W>* ent, uint32_t cnt,
+                            uint32_t lt, int plen, Acc& acc) {
+  const uint32_t lane = lane_id();
+  const uint32_t k = a.k;
+  for (uint32_t t0 = 0; t0 < cnt; t0 += 32) {
+    const uint32_t nb = min(32u, cnt - t0);
+    unsigned long long base_slot = 0;
+    if (a.cap) {
+      if (lane == 0) base_slot = atomicAdd(&a.acc[kAccWritten], (unsigned long long)nb);
+      base_slot = __shfl_sync(0xFFFFFFFFu, base_slot, 0);
+    }
+    if (lane < nb) {
+      const LIdx<W>* tp = ent + (size_t)(t0 + lane) * lt;
+      uint32_t ids[KMAX];
+      for (uint32_t j = 0; j < lt; j++) {  // insertion sort by original id
+        const uint32_t id = st.oid[tp[j]];
+        uint32_t q = j;
+        while (q > 0 && ids[q - 1] > id) {
+          ids[q] = ids[q - 1];
+          q--;
+        }
+        ids[q] = id;
+      }
+      const unsigned long long slot = base_slot + lane;
+      const bool wr = slot < a.cap;
+      uint32_t* o = a.out + slot * (unsigned long long)k;
+      uint64_t h = mix64(0x9E3779B97F4A7C15ull ^ (uint64_t)k);
+      int i = 0, q = 0;
+      uint32_t j = 0;
+      while (i < plen || j < lt) {
+        uint32_t y;
+        if (j >= lt || (i < plen && st.sid[i] < ids[j])) y = st.sid[i++];
+        else y = ids[j++];
+        h = mix64(h ^ (uint64_t)y);
+        if (wr) o[q] = y;
+        q++;
+      }
+      acc.sum += h;
+      acc.cnt += 1;
+    }
+  }
+  __syncwarp();
+}
+
+// Listing below the frame at depth `base` (set up by the caller: cand, pos,
+// the sorted prefix sid of length base + 1, dense[base]).  lar / lcap / *ltop:
+// this warp's arena, its size and the bytes this root has used.
+template <int W>
+__device__ void dfs_list_memo(WarpState<W>& st, const EnumKArgs& a, const Memo& memo, uint8_t* lar, uint32_t lcap,
+                              uint32_t* ltop, int base, Acc& acc) {
+  using T = LIdx<W>;
+  const uint32_t lane = lane_id();
+  const uint32_t k = a.k, need = k - 1;
+  int depth = base;
+  int rec = -1;  // depth of the frame being recorded
+  uint32_t rec_off = 0, rec_cnt = 0, rec_l = 0;
+  bool rec_ok = true;
+  // the base frame itself: a retrieval, or the start of a recording
+  {
+    const uint32_t l = need - base;
+    if (st.dense[base] && l >= 2 && memo.cap) {
+      uint32_t S[W], m = 0;
+#pragma unroll
+      for (int w = 0; w < W; w++) {
+        S[w] = st.cand[base * W + w];
+        m += __popc(S[w]);
+      }
+      unsigned long long v;
+      if (memo_find<W>(memo, S, l, &v)) {
+        acc.hits++;
+        list_replay<W>(st, a, (const T*)(lar + (v >> 24)), (uint32_t)(v & 0xFFFFFFull), l, base + 1, acc);
+        return;
+      }
+      const unsigned long long bound = (unsigned long long)binom_sat(m, l) * l * sizeof(T);
+      if (*ltop + bound <= lcap) {
+        rec = base;
+        rec_off = *ltop;
+        rec_cnt = 0;
+        rec_l = l;
+        rec_ok = true;
+      }
+    }
+  }
+  while (depth >= base) {
+    const uint32_t l = need - depth;  // vertices still to pick from cand[depth]
+    const uint32_t* S = st.cand + depth * W;
+    if (l == 1) {
+      // emit C ∪ {x} for each x in S: ids sorted, hashed, written; recorded
+      // as tuples (picks from the recorded frame down, then x) when recording
+      const int plen = depth + 1;
+#pragma unroll 1
+      for (int w = 0; w < W; w++) {
+        uint32_t x = S[w];
+        if (!x) continue;
+        const bool mine = (x >> lane) & 1u;
+        unsigned long long base_slot = 0;
+        if (a.cap) {
+          if (lane == 0) base_slot = atomicAdd(&a.acc[kAccWritten], (unsigned long long)__popc(x));
+          base_slot = __shfl_sync(0xFFFFFFFFu, base_slot, 0);
+        }
+        const uint32_t rank_in = __popc(x & lanemask_lt());
+        if (rec >= 0 && rec_ok) {
+          if ((unsigned long long)rec_off + (unsigned long long)(rec_cnt + __popc(x)) * rec_l * sizeof(T) > lcap) {
+            rec_ok = false;
+          } else if (mine) {
+            T* dst = (T*)(lar + rec_off) + (size_t)(rec_cnt + rank_in) * rec_l;
+            for (uint32_t j = 0; j + 1 < rec_l; j++) dst[j] = (T)st.cur[rec + j];
+            dst[rec_l - 1] = (T)((w << 5) + lane);
+          }
+          rec_cnt += __popc(x);
+        }
+        if (mine) {
+          const uint32_t id = st.oid[(w << 5) + lane];
+          const unsigned long long slot = base_slot + rank_in;
+          const bool wr = slot < a.cap;
+          uint32_t* o = a.out + slot * (unsigned long long)k;
+          uint64_t h = mix64(0x9E3779B97F4A7C15ull ^ (uint64_t)k);
+          int j = 0;
+          bool placed = false;
+          for (int q = 0; q < plen; q++) {
+            const uint32_t y = st.sid[q];
+            if (!placed && id < y) {
+              h = mix64(h ^ (uint64_t)id);
+              if (wr) o[j] = id;
+              j++;
+              placed = true;
+            }
+            h = mix64(h ^ (uint64_t)y);
+            if (wr) o[j] = y;
+            j++;
+          }
+          if (!placed) {
+            h = mix64(h ^ (uint64_t)id);
+            if (wr) o[j] = id;
+          }
+          acc.sum += h;
+          acc.cnt += 1;
+        }
+      }
+      __syncwarp();
+      depth--;
+      if (depth >= base) {
+        if (lane == 0)
+          for (int q = st.sins[depth]; q + 1 < depth + 2; q++) st.sid[q] = st.sid[q + 1];
+        __syncwarp();
+      }
+      continue;
+    }
+    const int v = next_desc<W>(S, st.masks + l * W, st.pos[depth]);
+    if (v < 0) {
+      if (depth == rec) {  // the recorded frame is complete: store its l-cliques
+        if (rec_ok) {
+          uint32_t key[W];
+#pragma unroll
+          for (int w = 0; w < W; w++) key[w] = S[w];
+          const int okk = memo_store<W>(memo, key, rec_l, ((unsigned long long)rec_off << 24) | rec_cnt);
+          acc.ins += okk;
+          acc.full += 1 - okk;
+          if (okk) *ltop = rec_off + ((rec_cnt * rec_l * (uint32_t)sizeof(T) + 3u) & ~3u);
+        }
+        rec = -1;
+      }
+      __syncwarp();
+      depth--;
+      if (depth >= base) {
+        if (lane == 0)
+          for (int q = st.sins[depth]; q + 1 < depth + 2; q++) st.sid[q] = st.sid[q + 1];
+        __syncwarp();
+      }
+      continue;
+    }
+    uint32_t c[W];
+    uint32_t sz = 0, anym = 0;
+    const uint32_t* rv = st.rows + (size_t)v * W;
+    const uint32_t* mk = st.masks + (l - 1) * W;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+      c[w] = S[w] & rv[w];
+      sz += __popc(c[w]);
+      anym |= c[w] & mk[w];
+    }
+    if (lane == 0) acc.ops += W;
+    __syncwarp();
+    if (lane == 0) st.pos[depth] = v - 1;
+    if (sz >= l - 1 && anym) {
+      const uint32_t cl = l - 1;
+      const bool cd = st.dense[depth] || (a.memo && cl > 3 && eq1_dense<W>(st, c, cl, sz, acc));
+      if (lane < W) st.cand[(depth + 1) * W + lane] = word_at<W>(c, lane);
+      if (lane == 0) {
+        st.pos[depth + 1] = top_bit<W>(c);
+        st.cur[depth] = v;
+        st.dense[depth + 1] = cd ? 1 : 0;
+        const uint32_t id = st.oid[v];
+        int q = depth + 1;
+        while (q > 0 && st.sid[q - 1] > id) {
+          st.sid[q] = st.sid[q - 1];
+          q--;
+        }
+        st.sid[q] = id;
+        st.sins[depth] = (uint8_t)q;
+      }
+      __syncwarp();
+      bool replayed = false;
+      if (cd && rec < 0 && cl >= 2 && memo.cap) {
+        unsigned long long ev;
+        if (memo_find<W>(memo, c, cl, &ev)) {
+          acc.hits++;
+          list_replay<W>(st, a, (const T*)(lar + (ev >> 24)), (uint32_t)(ev & 0xFFFFFFull), cl, depth + 2, acc);
+          replayed = true;
+        } else {
+          const unsigned long long bound = (unsigned long long)binom_sat(sz, cl) * cl * sizeof(T);
+          if (*ltop + bound <= lcap) {
+            rec = depth + 1;
+            rec_off = *ltop;
+            rec_cnt = 0;
+            rec_l = cl;
+            rec_ok = true;
+          }
+        }
+      }
+      if (replayed) {  // the child is resolved: take its pick back out of the prefix
+        if (lane == 0)
+          for (int q = st.sins[depth]; q + 1 < depth + 2; q++) st.sid[q] = st.sid[q + 1];
+        __syncwarp();
+        continue;
+      }
+      depth++;
+    }
+    __syncwarp();
+  }
+}
+
 // The searches are compiled once per width, in that width's translation
 // unit (kc_enum_w*.cu, relocatable device code), and called out of line from
 // every kernel: a width-W kernel also runs the narrow searches of smaller
@@ -886,6 +1163,9 @@ __device__ void dfs_plain_call(WarpState<W>& st, const EnumKArgs& a, int base, A
 template <int W>
 __device__ unsigned long long dfs_memo_call(WarpState<W>& st, const EnumKArgs& a, const Memo& memo, int base,
                                             Acc& acc);
+template <int W>
+__device__ void dfs_list_memo_call(WarpState<W>& st, const EnumKArgs& a, const Memo& memo, uint8_t* lar,
+                                   uint32_t lcap, uint32_t* ltop, int base, Acc& acc);
 
 #define KC_DFS_DECL(W)                                                                                    \
   template <>                                                                                             \
@@ -894,7 +1174,10 @@ __device__ unsigned long long dfs_memo_call(WarpState<W>& st, const EnumKArgs& a
   __device__ void dfs_plain_call<W, 1>(WarpState<W> & st, const EnumKArgs& a, int base, Acc& acc);       \
   template <>                                                                                             \
   __device__ unsigned long long dfs_memo_call<W>(WarpState<W> & st, const EnumKArgs& a, const Memo& memo, \
-                                                 int base, Acc& acc);
+                                                 int base, Acc& acc);                                     \
+  template <>                                                                                             \
+  __device__ void dfs_list_memo_call<W>(WarpState<W> & st, const EnumKArgs& a, const Memo& memo,         \
+                                        uint8_t* lar, uint32_t lcap, uint32_t* ltop, int base, Acc& acc);
 KC_DFS_DECL(1)
 KC_DFS_DECL(2)
 KC_DFS_DECL(4)
@@ -916,6 +1199,12 @@ KC_DFS_DECL(32)
   __device__ __noinline__ unsigned long long dfs_memo_call<W>(WarpState<W> & st, const EnumKArgs& a,            \
                                                               const Memo& memo, int base, Acc& acc) {           \
     return dfs_memo<W>(st, a, memo, base, acc);                                                                 \
+  }                                                                                                             \
+  template <>                                                                                                   \
+  __device__ __noinline__ void dfs_list_memo_call<W>(WarpState<W> & st, const EnumKArgs& a, const Memo& memo,   \
+                                                     uint8_t* lar, uint32_t lcap, uint32_t* ltop, int base,     \
+                                                     Acc& acc) {                                                \
+    dfs_list_memo<W>(st, a, memo, lar, lcap, ltop, base, acc);                                                  \
   }
 
 // The narrow state of a branch whose candidate set c (m vertices, in the
@@ -1065,37 +1354,48 @@ __device__ __noinline__ void run_branch(WarpState<W>& st, const EnumKArgs& a, co
   }
   // Eq. (1) for the branch's frame; below a dense frame every frame is
   // memoised (Algorithm 3 recurses into itself)
-  const bool cd = MODE == 2 && cl > 3 && (parent_dense || (a.memo && eq1_dense<W>(st, c, cl, sz, acc)));
-  if (MODE != 1 && cl >= 3 && cl <= kCompactMaxL && sz <= 32 && !cd) {
+  const bool cd = uses_trie(MODE) && cl > 3 && (parent_dense || (a.memo && eq1_dense<W>(st, c, cl, sz, acc)));
+  if (!is_list(MODE) && cl >= 3 && cl <= kCompactMaxL && sz <= 32 && !cd) {
     acc.cnt += count_compact<W>(st, c, sz, cl, acc.ops);
     return;
   }
-  if (MODE == 1 && lane == 0) {
+  if (is_list(MODE) && lane == 0) {
     uint32_t iu = a.vert[u], iv = a.vert[st.nbr[v1]];
     st.sid[0] = min(iu, iv);
     st.sid[1] = max(iu, iv);
   }
   if constexpr (compact_width(W) > 0) {
-    if (!cd && (MODE == 1 ? cl >= 2 : cl >= 3)) {
-      const int W2 = sz <= 32 ? 1 : (sz <= 64 ? 2 : (sz <= 128 ? 4 : 8));
-      if (2 * W2 <= W && W2 <= compact_width(W)) {
+    if (!cd && (is_list(MODE) ? cl >= 2 : cl >= 3)) {
+      // the narrowest width that holds the set: W2 words hold 32 * W2 vertices
+      const int W2 = sz <= 32 ? 1 : (sz <= 64 ? 2 : (sz <= 128 ? 4 : (sz <= 256 ? 8 : 16)));
+      if (2 * W2 <= W && W2 <= compact_width(W) && (int)sz <= 32 * W2) {
         __syncwarp();
-        if (MODE == 2 && memo2.cap == 0) narrow_dispatch<W, 0>(st, a, memo2, epoch2, c, (int)sz, W2, acc);
+        if (is_list(MODE)) narrow_dispatch<W, 1>(st, a, memo2, epoch2, c, (int)sz, W2, acc);
+        else if (MODE == 2 && memo2.cap == 0) narrow_dispatch<W, 0>(st, a, memo2, epoch2, c, (int)sz, W2, acc);
         else narrow_dispatch<W, MODE>(st, a, memo2, epoch2, c, (int)sz, W2, acc);
         return;
       }
     }
   }
-  if (MODE != 1 && cl <= 3) {
+  if (!is_list(MODE) && cl <= 3) {
     unsigned long long v = small_count<W>(st, c, cl, acc);
     if (lane == 0) acc.cnt += v;
     return;
   }
   if (lane < W) st.cand[W + lane] = word_at<W>(c, lane);
-  if (MODE == 1) {
+  if (MODE == 1 || (MODE == 3 && !cd)) {
     if (lane == 0) st.pos[1] = top_bit<W>(c);
     __syncwarp();
     dfs_plain_call<W, 1>(st, a, 1, acc);
+    return;
+  }
+  if (MODE == 3) {  // a dense branch: listed through the trie
+    if (lane == 0) {
+      st.pos[1] = top_bit<W>(c);
+      st.dense[1] = 1;
+    }
+    __syncwarp();
+    dfs_list_memo_call<W>(st, a, memo, memo.lar, memo.lcap, memo.ltop, 1, acc);
     return;
   }
   if (MODE == 0) {
@@ -1185,7 +1485,8 @@ __device__ bool publish_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, i
       while (x) {
         int b = __ffs(x) - 1;
         x &= x - 1;
-        if (idx++ >= skip) run_branch<W, MODE == 1 ? 1 : 0>(st, a, none, none2, &ep2, u, d, (w << 5) + b, acc, false);
+        if (idx++ >= skip) run_branch<W, is_list(MODE) ? 1 : 0>(st, a, none, none2, &ep2, u, d, (w << 5) + b, acc,
+                                                                   false);
       }
     }
   }
@@ -1235,6 +1536,10 @@ __device__ __forceinline__ void warp_memo(const EnumKArgs& a, Memo* m, Memo* m2)
   const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   *m = Memo{};
   *m2 = Memo{};
+  if (a.larena) {
+    m->lar = a.larena + gwarp * a.larena_bytes;
+    m->lcap = a.larena_bytes;
+  }
   if (!a.memo_cap) return;
   m->tags = a.memo_tags + gwarp * a.memo_cap;
   m->keys = a.memo_keys + gwarp * a.memo_cap * W;
@@ -1252,7 +1557,7 @@ __device__ __forceinline__ void warp_memo(const EnumKArgs& a, Memo* m, Memo* m2)
 
 
 // Phase 1: one warp per root, roots taken from the tier's list.
-// MODE 0: count (plain), 1: list, 2: count with memo.
+// MODE 0: count (plain), 1: list, 2: count with memo, 3: list with memo.
 // Everything for one root u of the graph in `a`: build, prune, then split,
 // count or list.  Counts accumulate in acc.cnt (lane-partial).
 template <int W, int MODE>
@@ -1267,14 +1572,19 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
   if (!kept) return;
   uint32_t S0[W];
   all_bits<W>(d, S0);
-  if (MODE == 2) {
+  if (uses_trie(MODE)) {
     next_epoch(memo, epoch);
     acc.ins_peak = max(acc.ins_peak, acc.ins - acc.ins_mark);
     acc.ins_mark = acc.ins;
+    if (MODE == 3) {
+      if (memo.ltop) *memo.ltop = 0;  // the arena holds this root's lists only
+      for (int i = lane; i < d; i += 32) st.oid[i] = a.vert[st.nbr[i]];
+      __syncwarp();
+    }
   }
   // Eq. (1) on G_u for the root frame
   bool dense0 = false;
-  if (MODE == 2 && a.memo && need > 3) {
+  if (uses_trie(MODE) && a.memo && need > 3) {
     uint32_t er = 0;
     for (int i = lane; i < d * W; i += 32) er += __popc(st.rows[i]);
     er = warp_sum(er);
@@ -1298,7 +1608,7 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
     const uint32_t thr = dense0 ? (a.split_wedges >> min(need - 4u, 12u)) : a.split_wedges;
     if (wg > thr && publish_root<W, MODE>(st, a, u, d, acc, d, dense0)) return;
   }
-  if (W >= 2 && (need >= 4 || (MODE == 1 && need >= 2))) {
+  if (W >= 2 && (need >= 4 || (is_list(MODE) && need >= 2))) {
     // the root frame of a wide root: one branch after another, from the
     // largest vertex down (the order of the identifying strings, so that a
     // dense branch resumes from its sibling's stored set), each searched in
@@ -1308,17 +1618,26 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
     const uint32_t* m1 = st.masks + need * W;
     for (int v1 = next_desc<W>(st.cand, m1, d - 1); v1 >= 0; v1 = next_desc<W>(st.cand, m1, v1 - 1))
       run_branch<W, MODE>(st, a, memo, memo2, epoch2, u, d, v1, acc, dense0);
-  } else if (MODE != 1 && need >= 2 && need <= kCompactMaxL && d <= 32 && !dense0) {
+  } else if (!is_list(MODE) && need >= 2 && need <= kCompactMaxL && d <= 32 && !dense0) {
     // the whole root at once: one word per row, lanes take the smallest vertex
     acc.cnt += count_compact<W>(st, S0, (uint32_t)d, need, acc.ops);
-  } else if (MODE == 0 || MODE == 1) {
+  } else if (MODE == 0 || MODE == 1 || (MODE == 3 && need < 2)) {
     if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
     if (lane == 0) {
       st.pos[0] = d - 1;
-      if (MODE == 1) st.sid[0] = a.vert[u];
+      if (is_list(MODE)) st.sid[0] = a.vert[u];
     }
     __syncwarp();
-    dfs_plain_call<W, MODE>(st, a, 0, acc);
+    dfs_plain_call<W, is_list(MODE) ? 1 : 0>(st, a, 0, acc);
+  } else if (MODE == 3) {
+    if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
+    if (lane == 0) {
+      st.pos[0] = d - 1;
+      st.sid[0] = a.vert[u];
+      st.dense[0] = dense0 ? 1 : 0;
+    }
+    __syncwarp();
+    dfs_list_memo_call<W>(st, a, memo, memo.lar, memo.lcap, memo.ltop, 0, acc);
   } else {
     if (need <= 3) {
       unsigned long long v = small_count<W>(st, S0, need, acc);
@@ -1355,7 +1674,7 @@ __device__ __forceinline__ void flush_query(const EnumKArgs& a, uint32_t q, Acc&
   const unsigned long long c = warp_sum(acc.cnt);
   acc.cnt = 0;
   if (lane_id() == 0 && c) atomicAdd(&a.bcount[q], c);
-  if (MODE == 1) {
+  if (is_list(MODE)) {
     const unsigned long long h = warp_sum(acc.sum);
     acc.sum = 0;
     if (lane_id() == 0 && h) atomicAdd(&a.bsum[q], h);
@@ -1364,7 +1683,7 @@ __device__ __forceinline__ void flush_query(const EnumKArgs& a, uint32_t q, Acc&
 
 // Phase 1: one warp per root, roots taken from the tier's list.  With a batch
 // (a.bq set) each list entry also names its query.
-// MODE 0: count (plain), 1: list, 2: count with memo.
+// MODE 0: count (plain), 1: list, 2: count with memo, 3: list with memo.
 template <int W, int MODE>
 __global__ void __launch_bounds__(256) k_enum(const __grid_constant__ EnumKArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -1374,6 +1693,8 @@ __global__ void __launch_bounds__(256) k_enum(const __grid_constant__ EnumKArgs 
   Acc acc;
   Memo memo, memo2;
   warp_memo<W>(a, &memo, &memo2);
+  uint32_t ltop = 0;
+  memo.ltop = &ltop;
   uint32_t epoch = 0, epoch2 = 0;
   while (true) {
     uint32_t qi = 0;
@@ -1412,6 +1733,8 @@ __global__ void __launch_bounds__(256) k_tasks(const __grid_constant__ EnumKArgs
   Acc acc;
   Memo memo, memo2;
   warp_memo<W>(a, &memo, &memo2);
+  uint32_t ltop = 0;
+  memo.ltop = &ltop;
   uint32_t epoch = 1u << 24, epoch2 = 1u << 24;  // above every epoch of phase 1
   const unsigned long long ntasks = min(*(volatile unsigned long long*)a.task_used, a.task_cap);
   unsigned long long cur = ~0ull;
@@ -1457,10 +1780,16 @@ __global__ void __launch_bounds__(256) k_tasks(const __grid_constant__ EnumKArgs
       }
       __syncwarp();
       cur = off;
-      if (MODE == 2) {
+      if (uses_trie(MODE)) {
         next_epoch(memo, &epoch);
         acc.ins_peak = max(acc.ins_peak, acc.ins - acc.ins_mark);
         acc.ins_mark = acc.ins;
+      }
+      if (MODE == 3) {
+        ltop = 0;
+        const uint32_t* vmap = a.bq ? b.vert : a.vert;
+        for (int i = lane; i < d; i += 32) st.oid[i] = vmap[st.nbr[i]];
+        __syncwarp();
       }
     }
     // the kernel's own arguments are read in place; only a batch binds a copy
@@ -1478,13 +1807,17 @@ __global__ void __launch_bounds__(256) k_tasks(const __grid_constant__ EnumKArgs
 __host__ __device__ constexpr int tier_words(int t) { return 1 << t; }
 
 // Kernel entry points of one width, for mode 0 (count), 1 (list), 2 (count
-// with the memo); each kc_enum_w*.cu instantiates one width with this.  With
-// MEMO 0 mode 2 would fall back to the count without the memo.
+// with the memo), 3 (list with the memo); each kc_enum_w*.cu instantiates one
+// width with this.  With MEMO 0 mode 2 would fall back to the count without
+// the memo.
 #define KC_TIER_KERNELS(W, MEMO)                                                 \
   void tier_kernels_w##W(int mode, const void** fe, const void** ft) {          \
     if (mode == 1) {                                                             \
       *fe = (const void*)k_enum<W, 1>;                                           \
       *ft = (const void*)k_tasks<W, 1>;                                          \
+    } else if (mode == 3) {                                                      \
+      *fe = (const void*)k_enum<W, 3>;                                           \
+      *ft = (const void*)k_tasks<W, 3>;                                          \
     } else if (mode == 2 && MEMO) {                                              \
       *fe = (const void*)k_enum<W, (MEMO ? 2 : 0)>;                              \
       *ft = (const void*)k_tasks<W, (MEMO ? 2 : 0)>;                             \

@@ -200,6 +200,45 @@ def test_chung_lu_small_tiers(ctx, ctx_plain, ctx_memo_only):
             c.free(h)
 
 
+@pytest.mark.parametrize("maker,ks,dense", [
+    (lambda: gg.chung_lu_planted(n=4000, n_cliques=6, smin=20, smax=30, seed=3), (6, 7), True),
+    (lambda: gg.complete(28), (6, 8), True),
+    (lambda: gg.turan(36, 12), (6, 7), True),
+    # neighbourhood density about 0.6: Eq. (1) never holds, the listing is plain
+    (lambda: gg.rgg_torus(3000, 40.0, seed=2), (6,), False),
+])
+def test_listing_trie_replays_and_matches_oracle(ctx, ctx_plain, maker, ks, dense):
+    """Listing with the device trie (Sec. IV, Algorithms 3-4): stored l-clique
+    lists of dense prefix subgraphs are replayed under other prefixes.  The
+    listed tuple set, total and checksum equal the oracle's with the memo on
+    and off; with it on, the trie is used (hits) and fewer candidate words
+    are intersected."""
+    g = maker()
+    og = oracle.OracleGraph.from_graph(g)
+    hs = [c.upload_host(g.n, g.rowptr, g.col) for c in (ctx, ctx_plain)]
+    try:
+        for k in ks:
+            want_c, want_s = og.checksum(k)
+            got = []
+            for c, h in zip((ctx, ctx_plain), hs):
+                arr, t, s = _list_all(c, h, k, want_c)
+                assert (t, s) == (want_c, want_s), (g.name, k)
+                got.append((arr, c.stats()))
+            if want_c <= 2_000_000:
+                exp = np.unique(og.list(k)[0], axis=0)
+                for arr, _ in got:
+                    u = np.unique(arr, axis=0)
+                    assert u.shape[0] == want_c  # no tuple twice
+                    assert np.array_equal(u, exp)
+            memo_st, plain_st = got[0][1], got[1][1]
+            if want_c and dense:
+                assert memo_st["memo_hits"] > 0, memo_st
+                assert memo_st["word_ops"] < plain_st["word_ops"], (memo_st["word_ops"], plain_st["word_ops"])
+    finally:
+        for c, h in zip((ctx, ctx_plain), hs):
+            c.free(h)
+
+
 @pytest.mark.parametrize("maker,splits", [
     (lambda: gg.chung_lu_planted(n=20000, n_cliques=40, seed=1), False),  # wide roots are dense: memo, no split
     (lambda: gg.rgg_torus(4000, 70.0, seed=6), True),

@@ -31,14 +31,24 @@ def _graphs():
     ]
 
 
+# Listing requests go up to this k: the planted-clique graph holds 1.7e10
+# 8-cliques, whose listing (hashing every clique) takes far longer than the
+# counts the rest of the mix asks for.
+LIST_KMAX = 5
+
+
 def _expected(c, hs, ks):
-    """(count, checksum) of every (graph, k) alone: kc_count and kc_list with cap 0."""
+    """(count, checksum) of every (graph, k) alone: kc_count, and kc_list with
+    cap 0 where the mix lists (checksum None elsewhere)."""
     table = {}
     for h in set(hs):
         for k in set(ks):
-            _, total, checksum = c.list(h, k, None, 0)
-            assert total == c.count(h, k)
-            table[(h, k)] = (total, checksum)
+            count = c.count(h, k)
+            checksum = None
+            if k <= LIST_KMAX:
+                _, total, checksum = c.list(h, k, None, 0)
+                assert total == count
+            table[(h, k)] = (count, checksum)
     return table
 
 
@@ -52,7 +62,7 @@ def test_results_same_alone_and_in_the_mix():
         rng = np.random.default_rng(0)
         n_req = 400
         modes = rng.integers(0, 2, n_req)
-        reqs = [(int(hs[i]), int(ks[j]), int(md)) for i, j, md in
+        reqs = [(int(hs[i]), int(ks[j]), int(md) if ks[j] <= LIST_KMAX else kc.KC_SERVE_COUNT) for i, j, md in
                 zip(rng.integers(0, len(hs), n_req), rng.integers(0, len(ks), n_req), modes)]
         tickets = [None] * len(reqs)
 
@@ -134,7 +144,7 @@ def _serve_inline(c, graphs, hs, huge, raw, cap):
     jobs = []
     for i, g in enumerate(graphs):
         for k in (3, 5, 7):
-            for mode in (kc.KC_SERVE_COUNT, kc.KC_SERVE_LIST):
+            for mode in (kc.KC_SERVE_COUNT, kc.KC_SERVE_LIST) if k <= LIST_KMAX else (kc.KC_SERVE_COUNT,):
                 jobs.append((kc.kc_serve_submit_csr(c.h, g.n, g.rowptr, g.col, k, mode=mode), g, k, mode))
                 jobs.append((kc.kc_serve_submit(c.h, hs[i], k, mode), g, k, mode))
     # a raw CSR that the lane must canonicalise
@@ -147,9 +157,10 @@ def _serve_inline(c, graphs, hs, huge, raw, cap):
         r = kc.kc_serve_wait(c.h, t, 120000)
         assert r is not None and r["status"] == kc.KC_OK, (g.name, k, mode, r)
         og = oracles.setdefault(id(g), oracle.OracleGraph.from_graph(g))
-        want = og.checksum(k)
-        assert r["count"] == want[0], (g.name, k)
-        assert r["checksum"] == (want[1] if mode == kc.KC_SERVE_LIST else 0), (g.name, k)
+        if mode == kc.KC_SERVE_LIST:
+            assert (r["count"], r["checksum"]) == og.checksum(k), (g.name, k)
+        else:
+            assert (r["count"], r["checksum"]) == (og.count(k)[0], 0), (g.name, k)
     r = kc.kc_serve_wait(c.h, t_huge, 120000)
     assert r["status"] == kc.KC_E_OOM
     st = kc.kc_serve_stats_get(c.h)

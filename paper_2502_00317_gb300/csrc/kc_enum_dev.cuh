@@ -343,9 +343,15 @@ __device__ __forceinline__ uint32_t tri_partial_body(const uint32_t (&S)[W], con
 // Widths of 8 words and more count triangles out of line (its unrolled
 // W x W body is large and is reached from several call sites).
 template <int W>
-__device__ __noinline__ uint32_t tri_partial_outlined(const uint32_t (&S)[W], const uint32_t* rows, const uint32_t* m3,
-                                                      uint32_t& ops) {
-  return tri_partial_body<W>(S, rows, m3, ops);
+__device__ __noinline__ uint32_t tri_partial_outlined(const uint32_t (&S_in)[W], const uint32_t* rows,
+                                                      const uint32_t* m3, uint32_t& ops_in) {
+  uint32_t S[W];
+#pragma unroll
+  for (int w = 0; w < W; w++) S[w] = S_in[w];
+  uint32_t ops = 0;
+  const uint32_t r = tri_partial_body<W>(S, rows, m3, ops);
+  ops_in += ops;
+  return r;
 }
 
 template <int W>
@@ -1185,27 +1191,84 @@ KC_DFS_DECL(8)
 KC_DFS_DECL(16)
 KC_DFS_DECL(32)
 
-// The definitions, for the width's own translation unit.
-#define KC_DFS_DEF(W)                                                                                           \
-  template <>                                                                                                   \
-  __device__ __noinline__ void dfs_plain_call<W, 0>(WarpState<W> & st, const EnumKArgs& a, int base, Acc& acc) { \
-    dfs_plain<W, 0>(st, a, base, acc);                                                                          \
-  }                                                                                                             \
-  template <>                                                                                                   \
-  __device__ __noinline__ void dfs_plain_call<W, 1>(WarpState<W> & st, const EnumKArgs& a, int base, Acc& acc) { \
-    dfs_plain<W, 1>(st, a, base, acc);                                                                          \
-  }                                                                                                             \
-  template <>                                                                                                   \
-  __device__ __noinline__ unsigned long long dfs_memo_call<W>(WarpState<W> & st, const EnumKArgs& a,            \
-                                                              const Memo& memo, int base, Acc& acc) {           \
-    return dfs_memo<W>(st, a, memo, base, acc);                                                                 \
-  }                                                                                                             \
-  template <>                                                                                                   \
-  __device__ __noinline__ void dfs_list_memo_call<W>(WarpState<W> & st, const EnumKArgs& a, const Memo& memo,   \
-                                                     uint8_t* lar, uint32_t lcap, uint32_t* ltop, int base,     \
-                                                     Acc& acc) {                                                \
-    dfs_list_memo<W>(st, a, memo, lar, lcap, ltop, base, acc);                                                  \
+// Adds the counters a search updates to the caller's accumulators.
+__device__ __forceinline__ void acc_add(Acc& to, const Acc& from) {
+  to.cnt += from.cnt;
+  to.sum += from.sum;
+  to.ops += from.ops;
+  to.hits += from.hits;
+  to.ins += from.ins;
+  to.full += from.full;
+  to.frames += from.frames;
+}
+
+// The definitions, for the width's own translation unit.  A search reached
+// out of line (a narrow subproblem of a wider root) works on a private copy
+// of the warp state's pointers and on fresh counters, added to the caller's
+// at the end, so that inside the search both live in registers.
+#define KC_DFS_DEF(W)                                                                                            \
+  template <>                                                                                                    \
+  __device__ __noinline__ void dfs_plain_call<W, 0>(WarpState<W> & st_in, const EnumKArgs& a, int base,         \
+                                                    Acc& acc_in) {                                               \
+    WarpState<W> st = st_in;                                                                                     \
+    Acc acc{};                                                                                                   \
+    dfs_plain<W, 0>(st, a, base, acc);                                                                           \
+    acc_add(acc_in, acc);                                                                                        \
+  }                                                                                                              \
+  template <>                                                                                                    \
+  __device__ __noinline__ void dfs_plain_call<W, 1>(WarpState<W> & st_in, const EnumKArgs& a, int base,         \
+                                                    Acc& acc_in) {                                               \
+    WarpState<W> st = st_in;                                                                                     \
+    Acc acc{};                                                                                                   \
+    dfs_plain<W, 1>(st, a, base, acc);                                                                           \
+    acc_add(acc_in, acc);                                                                                        \
+  }                                                                                                              \
+  template <>                                                                                                    \
+  __device__ __noinline__ unsigned long long dfs_memo_call<W>(WarpState<W> & st_in, const EnumKArgs& a,         \
+                                                              const Memo& memo_in, int base, Acc& acc_in) {      \
+    WarpState<W> st = st_in;                                                                                     \
+    const Memo memo = memo_in;                                                                                   \
+    Acc acc{};                                                                                                   \
+    const unsigned long long v = dfs_memo<W>(st, a, memo, base, acc);                                            \
+    acc_add(acc_in, acc);                                                                                        \
+    return v;                                                                                                    \
+  }                                                                                                              \
+  template <>                                                                                                    \
+  __device__ __noinline__ void dfs_list_memo_call<W>(WarpState<W> & st_in, const EnumKArgs& a,                  \
+                                                     const Memo& memo_in, uint8_t* lar, uint32_t lcap,           \
+                                                     uint32_t* ltop, int base, Acc& acc_in) {                    \
+    WarpState<W> st = st_in;                                                                                     \
+    const Memo memo = memo_in;                                                                                   \
+    Acc acc{};                                                                                                   \
+    uint32_t top = *ltop;                                                                                        \
+    dfs_list_memo<W>(st, a, memo, lar, lcap, &top, base, acc);                                                   \
+    *ltop = top;                                                                                                 \
+    acc_add(acc_in, acc);                                                                                        \
   }
+
+// The kernel's own width: inlined below 16 words (as one unit with the
+// kernel, the state and counters stay in registers); the wide widths go
+// out of line, where the unrolled 16- and 32-word loops would otherwise be
+// copied into every call site.
+template <int W, int MODE>
+__device__ __forceinline__ void dfs_plain_at(WarpState<W>& st, const EnumKArgs& a, int base, Acc& acc) {
+  if constexpr (W >= 16) dfs_plain_call<W, MODE>(st, a, base, acc);
+  else dfs_plain<W, MODE>(st, a, base, acc);
+}
+
+template <int W>
+__device__ __forceinline__ unsigned long long dfs_memo_at(WarpState<W>& st, const EnumKArgs& a, const Memo& memo,
+                                                          int base, Acc& acc) {
+  if constexpr (W >= 16) return dfs_memo_call<W>(st, a, memo, base, acc);
+  else return dfs_memo<W>(st, a, memo, base, acc);
+}
+
+template <int W>
+__device__ __forceinline__ void dfs_list_memo_at(WarpState<W>& st, const EnumKArgs& a, const Memo& memo, uint8_t* lar,
+                                                 uint32_t lcap, uint32_t* ltop, int base, Acc& acc) {
+  if constexpr (W >= 16) dfs_list_memo_call<W>(st, a, memo, lar, lcap, ltop, base, acc);
+  else dfs_list_memo<W>(st, a, memo, lar, lcap, ltop, base, acc);
+}
 
 // The narrow state of a branch whose candidate set c (m vertices, in the
 // root's width W) fits in W2 words: vertex j of the narrow state is the j-th
@@ -1327,9 +1390,9 @@ __device__ void narrow_dispatch(WarpState<W>& st, const EnumKArgs& a, Memo& memo
 // G_u ∩ N(v1).  A branch that is not dense by Eq. (1) and whose candidate set
 // fits a bit-matrix at most half as wide is searched in that narrow state.
 template <int W, int MODE>
-__device__ __noinline__ void run_branch(WarpState<W>& st, const EnumKArgs& a, const Memo& memo, Memo& memo2,
-                                        uint32_t* epoch2,
-                           uint32_t u, int d, int v1, Acc& acc, bool parent_dense) {
+__device__ __forceinline__ void run_branch_body(WarpState<W>& st, const EnumKArgs& a, const Memo& memo, Memo& memo2,
+                                                uint32_t* epoch2, uint32_t u, int d, int v1, Acc& acc,
+                                                bool parent_dense) {
   const uint32_t lane = lane_id();
   const uint32_t need = a.k - 1;
   uint32_t S0[W], c[W];
@@ -1386,7 +1449,7 @@ __device__ __noinline__ void run_branch(WarpState<W>& st, const EnumKArgs& a, co
   if (MODE == 1 || (MODE == 3 && !cd)) {
     if (lane == 0) st.pos[1] = top_bit<W>(c);
     __syncwarp();
-    dfs_plain_call<W, 1>(st, a, 1, acc);
+    dfs_plain_at<W, 1>(st, a, 1, acc);
     return;
   }
   if (MODE == 3) {  // a dense branch: listed through the trie
@@ -1395,13 +1458,13 @@ __device__ __noinline__ void run_branch(WarpState<W>& st, const EnumKArgs& a, co
       st.dense[1] = 1;
     }
     __syncwarp();
-    dfs_list_memo_call<W>(st, a, memo, memo.lar, memo.lcap, memo.ltop, 1, acc);
+    dfs_list_memo_at<W>(st, a, memo, memo.lar, memo.lcap, memo.ltop, 1, acc);
     return;
   }
   if (MODE == 0) {
     if (lane == 0) st.pos[1] = top_bit<W>(c);
     __syncwarp();
-    dfs_plain_call<W, 0>(st, a, 1, acc);
+    dfs_plain_at<W, 0>(st, a, 1, acc);
     return;
   }
   // MODE 2
@@ -1418,8 +1481,28 @@ __device__ __noinline__ void run_branch(WarpState<W>& st, const EnumKArgs& a, co
     st.fullins[1] = 0;
   }
   __syncwarp();
-  unsigned long long v = dfs_memo_call<W>(st, a, memo, 1, acc);
+  unsigned long long v = dfs_memo_at<W>(st, a, memo, 1, acc);
   if (lane == 0) acc.cnt += v;
+}
+
+// One branch: inlined below 16 words; out of line beyond, on a private
+// copy of the state's pointers and fresh counters (see the search wrappers).
+template <int W, int MODE>
+__device__ __noinline__ void run_branch_outlined(WarpState<W>& st_in, const EnumKArgs& a, const Memo& memo_in,
+                                                 Memo& memo2, uint32_t* epoch2, uint32_t u, int d, int v1,
+                                                 Acc& acc_in, bool parent_dense) {
+  WarpState<W> st = st_in;
+  const Memo memo = memo_in;
+  Acc acc{};
+  run_branch_body<W, MODE>(st, a, memo, memo2, epoch2, u, d, v1, acc, parent_dense);
+  acc_add(acc_in, acc);
+}
+
+template <int W, int MODE>
+__device__ __forceinline__ void run_branch(WarpState<W>& st, const EnumKArgs& a, const Memo& memo, Memo& memo2,
+                                           uint32_t* epoch2, uint32_t u, int d, int v1, Acc& acc, bool parent_dense) {
+  if constexpr (W >= 16) run_branch_outlined<W, MODE>(st, a, memo, memo2, epoch2, u, d, v1, acc, parent_dense);
+  else run_branch_body<W, MODE>(st, a, memo, memo2, epoch2, u, d, v1, acc, parent_dense);
 }
 
 // Heavy root: copy its built state to the arena and queue one task per
@@ -1628,7 +1711,7 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
       if (is_list(MODE)) st.sid[0] = a.vert[u];
     }
     __syncwarp();
-    dfs_plain_call<W, is_list(MODE) ? 1 : 0>(st, a, 0, acc);
+    dfs_plain_at<W, is_list(MODE) ? 1 : 0>(st, a, 0, acc);
   } else if (MODE == 3) {
     if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
     if (lane == 0) {
@@ -1637,7 +1720,7 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
       st.dense[0] = dense0 ? 1 : 0;
     }
     __syncwarp();
-    dfs_list_memo_call<W>(st, a, memo, memo.lar, memo.lcap, memo.ltop, 0, acc);
+    dfs_list_memo_at<W>(st, a, memo, memo.lar, memo.lcap, memo.ltop, 0, acc);
   } else {
     if (need <= 3) {
       unsigned long long v = small_count<W>(st, S0, need, acc);
@@ -1651,7 +1734,7 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
         st.fullins[0] = 0;
       }
       __syncwarp();
-      unsigned long long v = dfs_memo_call<W>(st, a, memo, 0, acc);
+      unsigned long long v = dfs_memo_at<W>(st, a, memo, 0, acc);
       if (lane == 0) acc.cnt += v;
     }
   }

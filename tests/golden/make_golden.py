@@ -5,6 +5,7 @@
     python tests/golden/make_golden.py chunglu [k ...]   # Chung-Lu + planted, k=5..9 counts
     python tests/golden/make_golden.py rmat [k ...]      # R-MAT scale 22, count + checksum (default k=3,4)
     python tests/golden/make_golden.py rmatcount k ...   # R-MAT scale 22, count only
+    python tests/golden/make_golden.py rmatscale S k ... # R-MAT scale S (config-3 parameters), count + checksum
 
 Every expected value comes from ``oracle`` on inputs from the seeded
 generator module; nothing here touches the CUDA path.
@@ -83,6 +84,13 @@ if __name__ == "__main__":
         chunglu([int(x) for x in sys.argv[2:]] or [5, 6, 7, 8, 9])
     elif what == "rmat":
         rmat([int(x) for x in sys.argv[2:]] or [3, 4])
+    elif what == "rmatscale":
+        # config 3's generator at a scale the oracle lists in minutes (scale 14: about 1 min,
+        # scale 16: about 11 min on 8 cores for k = 6)
+        scale = int(sys.argv[2])
+        g = gg.rmat(scale=scale, edge_factor=16, seed=2)
+        _record("config_results.json", f"rmat_{scale}_16_seed2", oracle.OracleGraph.from_graph(g), g,
+                [int(x) for x in sys.argv[3:]] or [6], True)
     elif what == "rmatcount":
         g = gg.config_rmat()
         _record("config_results.json", "rmat_22_16_seed2", oracle.OracleGraph.from_graph(g), g,

@@ -556,3 +556,45 @@ def test_rmat_scale22_full_size_vs_golden(ctx):
         assert (tot, chk) == (gold["rmat_22_16_seed2_k4"]["count"], gold["rmat_22_16_seed2_k4"]["checksum"])
     finally:
         ctx.free(h)
+
+
+@pytest.mark.parametrize("opts", [{}, {"no_memo": True}, {"no_prune": True}, {"split_threshold": 1},
+                                  {"decomposition": kc.KC_EDGE_PARALLEL}])
+def test_rmat_k6_vs_oracle(opts):
+    """Config 3's generator (R-MAT, edge factor 16, (0.57, 0.19, 0.19, 0.05),
+    seed 2, raw pairs canonicalised on the device) at scale 14, where the
+    oracle lists every 6-clique: count, total and checksum of the listing,
+    and the listing split into root ranges whose totals add and checksums
+    wrap-add to the whole; with the memo, pruning, heavy-root split and
+    decomposition toggled.  At scale 16, the default settings: count and
+    checksum against the oracle's."""
+    gold = json.load(open(os.path.join(GOLD, "config_results.json")))
+    c = kc.Context(0, **opts)
+    try:
+        for scale, list_it in ((14, True), (16, not opts)):
+            key = f"rmat_{scale}_16_seed2_k6"
+            if key not in gold:
+                continue
+            want = gold[key]
+            g = gg.rmat(scale=scale, edge_factor=16, seed=2)
+            assert want["fingerprint"] == g.fingerprint()
+            h = c.upload_host(g.n, g.rowptr, g.col, canonicalize=True)
+            try:
+                assert c.info(h)["degeneracy"] == want["degeneracy"]
+                assert c.count(h, 6) == want["count"], (scale, opts)
+                if not list_it:
+                    continue
+                assert c.list(h, 6, None, 0)[1:] == (want["count"], want["checksum"]), (scale, opts)
+                if scale == 14:
+                    n = g.n
+                    cuts = [0, n // 3, n - 3000, n - 800, n - 100, n]
+                    tot, chk = 0, 0
+                    for lo, hi in zip(cuts, cuts[1:]):
+                        _, t, s = c.list_range(h, 6, lo, hi)
+                        tot += t
+                        chk = (chk + s) % (1 << 64)
+                    assert (tot, chk) == (want["count"], want["checksum"]), opts
+            finally:
+                c.free(h)
+    finally:
+        c.close()

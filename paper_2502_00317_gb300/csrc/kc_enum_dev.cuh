@@ -1333,7 +1333,7 @@ __device__ void build_compact(const WarpState<W>& st, WarpState<W2>& cs, const u
 // narrow vertex; the clique prefix (root and v1) comes from the wide state.
 template <int W, int W2, int MODE>
 __device__ void run_narrow(WarpState<W>& st, const EnumKArgs& a, Memo& memo2, uint32_t* epoch2,
-                           const uint32_t (&c)[W], int m, Acc& acc) {
+                           const uint32_t (&c)[W], int m, bool dense, Acc& acc) {
   const uint32_t lane = lane_id();
   WarpState<W2> cs;
   cs.carve(st.cbase, (int)a.depth);
@@ -1348,7 +1348,7 @@ __device__ void run_narrow(WarpState<W>& st, const EnumKArgs& a, Memo& memo2, ui
       cs.sid[1] = st.sid[1];
     }
     cs.sum[1] = 0;
-    cs.dense[1] = 0;
+    cs.dense[1] = dense ? 1 : 0;  // a dense frame memoises from the start (Algorithm 3)
     cs.fullins[1] = 0;
   }
   __syncwarp();
@@ -1363,25 +1363,25 @@ __device__ void run_narrow(WarpState<W>& st, const EnumKArgs& a, Memo& memo2, ui
 
 template <int W, int MODE>
 __device__ void narrow_dispatch(WarpState<W>& st, const EnumKArgs& a, Memo& memo2, uint32_t* epoch2,
-                                const uint32_t (&c)[W], int m, int W2, Acc& acc) {
+                                const uint32_t (&c)[W], int m, int W2, bool dense, Acc& acc) {
   if (W2 == 1) {
-    run_narrow<W, 1, MODE>(st, a, memo2, epoch2, c, m, acc);
+    run_narrow<W, 1, MODE>(st, a, memo2, epoch2, c, m, dense, acc);
     return;
   }
   if constexpr (compact_width(W) >= 2) {
     if (W2 == 2) {
-      run_narrow<W, 2, MODE>(st, a, memo2, epoch2, c, m, acc);
+      run_narrow<W, 2, MODE>(st, a, memo2, epoch2, c, m, dense, acc);
       return;
     }
   }
   if constexpr (compact_width(W) >= 4) {
     if (W2 == 4) {
-      run_narrow<W, 4, MODE>(st, a, memo2, epoch2, c, m, acc);
+      run_narrow<W, 4, MODE>(st, a, memo2, epoch2, c, m, dense, acc);
       return;
     }
   }
   if constexpr (compact_width(W) >= 8) {
-    if (W2 == 8) run_narrow<W, 8, MODE>(st, a, memo2, epoch2, c, m, acc);
+    if (W2 == 8) run_narrow<W, 8, MODE>(st, a, memo2, epoch2, c, m, dense, acc);
   }
 }
 
@@ -1428,14 +1428,18 @@ __device__ __forceinline__ void run_branch_body(WarpState<W>& st, const EnumKArg
     st.sid[1] = max(iu, iv);
   }
   if constexpr (compact_width(W) > 0) {
-    if (!cd && (is_list(MODE) ? cl >= 2 : cl >= 3)) {
+    // a dense branch of a root of 16 or 32 words is narrowed too, with its
+    // trie in the narrow index space: the branch's own frames still share
+    // their entries, and every intersection shrinks to a few words
+    const bool narrow_dense = cd && W >= 16 && MODE == 2 && memo2.cap != 0;
+    if ((!cd || narrow_dense) && (is_list(MODE) ? cl >= 2 : cl >= 3)) {
       // the narrowest width that holds the set: W2 words hold 32 * W2 vertices
       const int W2 = sz <= 32 ? 1 : (sz <= 64 ? 2 : (sz <= 128 ? 4 : (sz <= 256 ? 8 : 16)));
       if (2 * W2 <= W && W2 <= compact_width(W) && (int)sz <= 32 * W2) {
         __syncwarp();
-        if (is_list(MODE)) narrow_dispatch<W, 1>(st, a, memo2, epoch2, c, (int)sz, W2, acc);
-        else if (MODE == 2 && memo2.cap == 0) narrow_dispatch<W, 0>(st, a, memo2, epoch2, c, (int)sz, W2, acc);
-        else narrow_dispatch<W, MODE>(st, a, memo2, epoch2, c, (int)sz, W2, acc);
+        if (is_list(MODE)) narrow_dispatch<W, 1>(st, a, memo2, epoch2, c, (int)sz, W2, false, acc);
+        else if (MODE == 2 && memo2.cap == 0) narrow_dispatch<W, 0>(st, a, memo2, epoch2, c, (int)sz, W2, false, acc);
+        else narrow_dispatch<W, MODE>(st, a, memo2, epoch2, c, (int)sz, W2, cd, acc);
         return;
       }
     }

@@ -22,6 +22,13 @@ SOURCES = ["kc_api.cu", "kc_prep.cu", "kc_enum.cu", "kc_serve.cu", "kc_enum_w1.c
 PEAK_SOURCE = "kc_peak.cu"  # separate library: the benchmark's integer-pipe peak
 PEAK_LIB = os.path.join(BUILD, "libkc_peak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Register caps of the enumerator units.  The kernels of widths up to 4 words
+# are bounded to about 85 registers, wider ones to 128 (kc_block_threads /
+# kc_min_blocks); the searches of a width are also called out of line by the
+# kernels of wider roots (their narrow subproblems), so each unit is capped at
+# the smallest bound among its callers.
+MAXRREG = {"kc_enum_w1.cu": 80, "kc_enum_w2.cu": 80, "kc_enum_w4.cu": 128, "kc_enum_w8.cu": 128,
+           "kc_enum_w16.cu": 128, "kc_enum_w32.cu": 128}
 
 
 def nvcc() -> str:
@@ -42,7 +49,7 @@ def _digest() -> str:
         if os.path.isfile(p):
             h.update(name.encode())
             h.update(open(p, "rb").read())
-    h.update(" ".join(_flags() + ["-rdc=true"]).encode())
+    h.update(" ".join(_flags() + ["-rdc=true"] + [f"{k}:{v}" for k, v in sorted(MAXRREG.items())]).encode())
     return h.hexdigest()
 
 
@@ -73,7 +80,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
         # relocatable device code: each width's searches are compiled once, in
         # its own unit, and called from the kernels of every other width
-        cmd = [cc, *_flags(extra_flags), "-rdc=true", "-c", os.path.join(CSRC, src), "-o", obj]
+        cap = [f"-maxrregcount={MAXRREG[src]}"] if src in MAXRREG else []
+        cmd = [cc, *_flags(extra_flags), "-rdc=true", *cap, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

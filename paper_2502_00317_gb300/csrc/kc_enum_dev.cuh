@@ -92,6 +92,13 @@ __host__ __device__ constexpr size_t warp_state_raw(int W, int D) {
 // Per-warp stride of that state (16-byte aligned).
 __host__ __device__ constexpr size_t warp_state_stride(int W, int D) { return (warp_state_raw(W, D) + 15) & ~(size_t)15; }
 
+// Threads per block of the width-W kernels (8 warps up to 4 words, 4 beyond)
+// and the blocks per SM their register budget is sized for: the searches are
+// latency-bound, so the kernels keep to about 85 registers (W <= 4) or 128
+// (W >= 8) to keep 24 and 16 warps resident per SM.
+__host__ __device__ constexpr int kc_block_threads(int W) { return W <= 4 ? 256 : 128; }
+__host__ __device__ constexpr int kc_min_blocks(int W) { return W <= 4 ? 3 : 4; }
+
 // Width of the narrow bit-matrix a branch of a width-W root is re-indexed
 // into when its candidate set is small (0: none).  The narrow state lives in
 // shared memory after the root's own.
@@ -100,7 +107,8 @@ __host__ __device__ constexpr int compact_width(int W) { return W >= 16 ? 8 : W 
 // Shared-memory bytes per warp of a width-W kernel: the root's state (widths
 // up to 8; wider ones keep it in global memory) and the narrow branch state.
 __host__ __device__ constexpr size_t warp_smem_bytes(int W, int D) {
-  return (W <= 8 ? warp_state_stride(W, D) : 0) + (compact_width(W) ? warp_state_stride(compact_width(W), D) : 0);
+  return (W <= 8 ? warp_state_stride(W, D) : 0) + (compact_width(W) ? warp_state_stride(compact_width(W), D) : 0) +
+         64;  // the warp's per-root counters (WarpStat)
 }
 
 // Per-warp working state, carved from shared or global memory.
@@ -122,6 +130,7 @@ struct WarpState {
   uint8_t* fullins;           // [D] frame's whole set already stored
   uint32_t* crow;             // [32] rows of a candidate set re-indexed to 0..31 (count_compact)
   uint8_t* cbase;             // this warp's narrow branch state (shared memory), or nullptr
+  unsigned long long* stats;  // [kWsCount] this warp's per-root counters (shared memory; lane 0)
   __device__ void carve(uint8_t* base, int D) {
     uint8_t* p = base;
     sum = (unsigned long long*)p; p += (size_t)D * 8;
@@ -140,6 +149,7 @@ struct WarpState {
     dense = p; p += D;
     fullins = p;
     cbase = nullptr;
+    stats = nullptr;
   }
 };
 
@@ -404,9 +414,21 @@ struct Acc {
   unsigned long long cnt = 0, sum = 0;
   uint32_t ops = 0;          // candidate words intersected since the last fold into ops64
   unsigned long long ops64 = 0;
-  unsigned long long pruned = 0, words = 0, hits = 0, ins = 0, full = 0, frames = 0, heavy = 0, tasks = 0;
-  unsigned long long build_ns = 0, busy_ns = 0;  // warp time (lane 0's account) in builds, and in all
-  unsigned long long ins_mark = 0, ins_peak = 0; // trie entries of the current root: inserts since ins_mark
+  unsigned long long hits = 0, ins = 0, full = 0, frames = 0;
+};
+
+// Counters updated once per root or task, kept by lane 0 in the warp's
+// shared memory instead of registers.
+enum WarpStat : int {
+  kWsPruned = 0,  // roots dropped by the soft-embedding test
+  kWsWords,       // DAG words read by the builds
+  kWsHeavy,       // roots published to the split path
+  kWsTasks,       // tasks queued
+  kWsBuildNs,     // nanoseconds in builds
+  kWsBusyNs,      // nanoseconds on roots and tasks
+  kWsInsMark,     // trie inserts when the current root started
+  kWsInsPeak,     // most trie inserts of one root
+  kWsCount
 };
 
 // Steps 1 and 2 for root u: bitmap rows, Algorithm 5, masks.  Returns false
@@ -465,7 +487,8 @@ __device__ bool build_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, int
       words += (uint32_t)(p - b);
     }
   }
-  acc.words += words;
+  words = warp_sum(words);
+  if (lane == 0) st.stats[kWsWords] += words;
   __syncwarp();
   // Algorithm 5 on G[N(u) ∪ {u}], r capped at k
   const uint32_t rcap = k;
@@ -493,7 +516,7 @@ __device__ bool build_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, int
     root_r = __shfl_sync(0xFFFFFFFFu, root_r, 0);
     __syncwarp();
     if (root_r < k) {
-      acc.pruned++;
+      if (lane == 0) st.stats[kWsPruned]++;
       return false;
     }
   } else {
@@ -1203,33 +1226,29 @@ __device__ __forceinline__ void acc_add(Acc& to, const Acc& from) {
 }
 
 // The definitions, for the width's own translation unit.  A search reached
-// out of line (a narrow subproblem of a wider root) works on a private copy
-// of the warp state's pointers and on fresh counters, added to the caller's
-// at the end, so that inside the search both live in registers.
+// out of line (a narrow subproblem of a wider root, or a wide width) works on
+// fresh counters, added to the caller's at the end, so that inside the
+// search they live in registers.
 #define KC_DFS_DEF(W)                                                                                            \
   template <>                                                                                                    \
   __device__ __noinline__ void dfs_plain_call<W, 0>(WarpState<W> & st_in, const EnumKArgs& a, int base,         \
                                                     Acc& acc_in) {                                               \
-    WarpState<W> st = st_in;                                                                                     \
     Acc acc{};                                                                                                   \
-    dfs_plain<W, 0>(st, a, base, acc);                                                                           \
+    dfs_plain<W, 0>(st_in, a, base, acc);                                                                           \
     acc_add(acc_in, acc);                                                                                        \
   }                                                                                                              \
   template <>                                                                                                    \
   __device__ __noinline__ void dfs_plain_call<W, 1>(WarpState<W> & st_in, const EnumKArgs& a, int base,         \
                                                     Acc& acc_in) {                                               \
-    WarpState<W> st = st_in;                                                                                     \
     Acc acc{};                                                                                                   \
-    dfs_plain<W, 1>(st, a, base, acc);                                                                           \
+    dfs_plain<W, 1>(st_in, a, base, acc);                                                                           \
     acc_add(acc_in, acc);                                                                                        \
   }                                                                                                              \
   template <>                                                                                                    \
   __device__ __noinline__ unsigned long long dfs_memo_call<W>(WarpState<W> & st_in, const EnumKArgs& a,         \
                                                               const Memo& memo_in, int base, Acc& acc_in) {      \
-    WarpState<W> st = st_in;                                                                                     \
-    const Memo memo = memo_in;                                                                                   \
     Acc acc{};                                                                                                   \
-    const unsigned long long v = dfs_memo<W>(st, a, memo, base, acc);                                            \
+    const unsigned long long v = dfs_memo<W>(st_in, a, memo_in, base, acc);                                            \
     acc_add(acc_in, acc);                                                                                        \
     return v;                                                                                                    \
   }                                                                                                              \
@@ -1237,11 +1256,9 @@ __device__ __forceinline__ void acc_add(Acc& to, const Acc& from) {
   __device__ __noinline__ void dfs_list_memo_call<W>(WarpState<W> & st_in, const EnumKArgs& a,                  \
                                                      const Memo& memo_in, uint8_t* lar, uint32_t lcap,           \
                                                      uint32_t* ltop, int base, Acc& acc_in) {                    \
-    WarpState<W> st = st_in;                                                                                     \
-    const Memo memo = memo_in;                                                                                   \
     Acc acc{};                                                                                                   \
     uint32_t top = *ltop;                                                                                        \
-    dfs_list_memo<W>(st, a, memo, lar, lcap, &top, base, acc);                                                   \
+    dfs_list_memo<W>(st_in, a, memo_in, lar, lcap, &top, base, acc);                                                   \
     *ltop = top;                                                                                                 \
     acc_add(acc_in, acc);                                                                                        \
   }
@@ -1489,16 +1506,14 @@ __device__ __forceinline__ void run_branch_body(WarpState<W>& st, const EnumKArg
   if (lane == 0) acc.cnt += v;
 }
 
-// One branch: inlined below 16 words; out of line beyond, on a private
-// copy of the state's pointers and fresh counters (see the search wrappers).
+// One branch: inlined below 16 words; out of line beyond, on fresh
+// counters (see the search wrappers).
 template <int W, int MODE>
 __device__ __noinline__ void run_branch_outlined(WarpState<W>& st_in, const EnumKArgs& a, const Memo& memo_in,
                                                  Memo& memo2, uint32_t* epoch2, uint32_t u, int d, int v1,
                                                  Acc& acc_in, bool parent_dense) {
-  WarpState<W> st = st_in;
-  const Memo memo = memo_in;
   Acc acc{};
-  run_branch_body<W, MODE>(st, a, memo, memo2, epoch2, u, d, v1, acc, parent_dense);
+  run_branch_body<W, MODE>(st_in, a, memo_in, memo2, epoch2, u, d, v1, acc, parent_dense);
   acc_add(acc_in, acc);
 }
 
@@ -1559,8 +1574,10 @@ __device__ bool publish_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, i
     done += __popc(x);
   }
   __threadfence();
-  acc.heavy++;
-  acc.tasks += nt;
+  if (lane == 0) {
+    st.stats[kWsHeavy]++;
+    st.stats[kWsTasks] += nt;
+  }
   // branches past the queue's capacity stay with this warp
   if (t0 + nt > a.task_cap) {
     Memo none{}, none2{};
@@ -1581,27 +1598,26 @@ __device__ bool publish_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, i
 }
 
 template <int W>
-__device__ void flush_acc(const EnumKArgs& a, Acc& acc) {
+__device__ void flush_acc(const EnumKArgs& a, Acc& acc, const unsigned long long* ws) {
   const uint32_t lane = lane_id();
   unsigned long long cnt = warp_sum(acc.cnt);
   unsigned long long sum = warp_sum(acc.sum);
-  unsigned long long words = warp_sum(acc.words);
   unsigned long long ops = warp_sum(acc.ops64 + acc.ops);
   if (lane == 0) {
     if (ops) atomicAdd(&a.acc[kAccWordOps], ops);
     if (cnt) atomicAdd(&a.acc[kAccCount], cnt);
     if (sum) atomicAdd(&a.acc[kAccChecksum], sum);
-    if (acc.pruned) atomicAdd(&a.acc[kAccRootsPruned], acc.pruned);
-    if (words) atomicAdd(&a.acc[kAccBuildWords], words);
+    if (ws[kWsPruned]) atomicAdd(&a.acc[kAccRootsPruned], ws[kWsPruned]);
+    if (ws[kWsWords]) atomicAdd(&a.acc[kAccBuildWords], ws[kWsWords]);
     if (acc.hits) atomicAdd(&a.acc[kAccMemoHits], acc.hits);
     if (acc.ins) atomicAdd(&a.acc[kAccMemoInserts], acc.ins);
     if (acc.full) atomicAdd(&a.acc[kAccMemoFull], acc.full);
     if (acc.frames) atomicAdd(&a.acc[kAccMemoFrames], acc.frames);
-    if (acc.heavy) atomicAdd(&a.acc[kAccRootsHeavy], acc.heavy);
-    if (acc.tasks) atomicAdd(&a.acc[kAccTasks], acc.tasks);
-    if (acc.build_ns) atomicAdd(&a.acc[kAccBuildNs], acc.build_ns);
-    if (acc.busy_ns) atomicAdd(&a.acc[kAccBusyNs], acc.busy_ns);
-    const unsigned long long peak = max(acc.ins_peak, acc.ins - acc.ins_mark);
+    if (ws[kWsHeavy]) atomicAdd(&a.acc[kAccRootsHeavy], ws[kWsHeavy]);
+    if (ws[kWsTasks]) atomicAdd(&a.acc[kAccTasks], ws[kWsTasks]);
+    if (ws[kWsBuildNs]) atomicAdd(&a.acc[kAccBuildNs], ws[kWsBuildNs]);
+    if (ws[kWsBusyNs]) atomicAdd(&a.acc[kAccBusyNs], ws[kWsBusyNs]);
+    const unsigned long long peak = max(ws[kWsInsPeak], acc.ins - ws[kWsInsMark]);
     if (peak) atomicMax(&a.acc[kAccMemoPeak], peak);
   }
 }
@@ -1613,6 +1629,9 @@ __device__ __forceinline__ void carve_state(WarpState<W>& st, const EnumKArgs& a
   if (a.gstate) st.carve(a.gstate + gwarp * a.gstride, (int)a.depth);
   else st.carve(mine, (int)a.depth);
   if (compact_width(W)) st.cbase = mine + a.coff;
+  st.stats = (unsigned long long*)(mine + a.sstride - 64);
+  if (lane_id() < kWsCount) st.stats[lane_id()] = 0ull;
+  __syncwarp();
 }
 
 // This warp's memo tables.  With a narrow branch state the table is halved:
@@ -1655,14 +1674,16 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
   const int d = (int)(a.orow[u + 1] - a.orow[u]);
   const unsigned long long tb = global_ns();
   const bool kept = build_root<W>(st, a, u, d, acc);
-  if (lane == 0) acc.build_ns += global_ns() - tb;
+  if (lane == 0) st.stats[kWsBuildNs] += global_ns() - tb;
   if (!kept) return;
   uint32_t S0[W];
   all_bits<W>(d, S0);
   if (uses_trie(MODE)) {
     next_epoch(memo, epoch);
-    acc.ins_peak = max(acc.ins_peak, acc.ins - acc.ins_mark);
-    acc.ins_mark = acc.ins;
+    if (lane == 0) {
+      st.stats[kWsInsPeak] = max(st.stats[kWsInsPeak], acc.ins - st.stats[kWsInsMark]);
+      st.stats[kWsInsMark] = acc.ins;
+    }
     if (MODE == 3) {
       if (memo.ltop) *memo.ltop = 0;  // the arena holds this root's lists only
       for (int i = lane; i < d; i += 32) st.oid[i] = a.vert[st.nbr[i]];
@@ -1772,7 +1793,7 @@ __device__ __forceinline__ void flush_query(const EnumKArgs& a, uint32_t q, Acc&
 // (a.bq set) each list entry also names its query.
 // MODE 0: count (plain), 1: list, 2: count with memo, 3: list with memo.
 template <int W, int MODE>
-__global__ void __launch_bounds__(256) k_enum(const __grid_constant__ EnumKArgs a) {
+__global__ void __launch_bounds__(kc_block_threads(W), kc_min_blocks(W)) k_enum(const __grid_constant__ EnumKArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = lane_id();
   WarpState<W> st;
@@ -1799,18 +1820,18 @@ __global__ void __launch_bounds__(256) k_enum(const __grid_constant__ EnumKArgs 
     } else {
       root_body<W, MODE>(st, a, memo, &epoch, memo2, &epoch2, u, acc);
     }
-    if (lane == 0) acc.busy_ns += global_ns() - t0;
+    if (lane == 0) st.stats[kWsBusyNs] += global_ns() - t0;
     acc.ops64 += acc.ops;
     acc.ops = 0;
     __syncwarp();
   }
-  flush_acc<W>(a, acc);
+  flush_acc<W>(a, acc, st.stats);
 }
 
 // Phase 2: the split path.  Every warp takes (root, v1) tasks; a root's built
 // state is loaded from the arena when the task's root changes.
 template <int W, int MODE>
-__global__ void __launch_bounds__(256) k_tasks(const __grid_constant__ EnumKArgs a) {
+__global__ void __launch_bounds__(kc_block_threads(W), kc_min_blocks(W)) k_tasks(const __grid_constant__ EnumKArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = lane_id();
   WarpState<W> st;
@@ -1869,8 +1890,10 @@ __global__ void __launch_bounds__(256) k_tasks(const __grid_constant__ EnumKArgs
       cur = off;
       if (uses_trie(MODE)) {
         next_epoch(memo, &epoch);
-        acc.ins_peak = max(acc.ins_peak, acc.ins - acc.ins_mark);
-        acc.ins_mark = acc.ins;
+        if (lane == 0) {
+          st.stats[kWsInsPeak] = max(st.stats[kWsInsPeak], acc.ins - st.stats[kWsInsMark]);
+          st.stats[kWsInsMark] = acc.ins;
+        }
       }
       if (MODE == 3) {
         ltop = 0;
@@ -1882,12 +1905,12 @@ __global__ void __launch_bounds__(256) k_tasks(const __grid_constant__ EnumKArgs
     // the kernel's own arguments are read in place; only a batch binds a copy
     run_branch<W, MODE>(st, a.bq ? b : a, memo, memo2, &epoch2, u, d, v1, acc, dense);
     if (a.bq) flush_query<MODE>(a, b.query, acc);
-    if (lane == 0) acc.busy_ns += global_ns() - t0;
+    if (lane == 0) st.stats[kWsBusyNs] += global_ns() - t0;
     acc.ops64 += acc.ops;
     acc.ops = 0;
     __syncwarp();
   }
-  flush_acc<W>(a, acc);
+  flush_acc<W>(a, acc, st.stats);
 }
 
 // Bitmap words of width tier t: 1, 2, 4, ..., 32 words.

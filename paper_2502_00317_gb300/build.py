@@ -22,12 +22,12 @@ SOURCES = ["kc_api.cu", "kc_prep.cu", "kc_enum.cu", "kc_serve.cu", "kc_enum_w1.c
 PEAK_SOURCE = "kc_peak.cu"  # separate library: the benchmark's integer-pipe peak
 PEAK_LIB = os.path.join(BUILD, "libkc_peak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# Register caps of the enumerator units.  The kernels of widths up to 4 words
-# are bounded to about 85 registers, wider ones to 128 (kc_block_threads /
-# kc_min_blocks); the searches of a width are also called out of line by the
-# kernels of wider roots (their narrow subproblems), so each unit is capped at
-# the smallest bound among its callers.
-MAXRREG = {"kc_enum_w1.cu": 80, "kc_enum_w2.cu": 80, "kc_enum_w4.cu": 128, "kc_enum_w8.cu": 128,
+# Register caps of the enumerator units.  The kernels of widths 1 and 2 are
+# bounded to 64 registers, width 4 to about 85, wider ones to 128
+# (kc_block_threads / kc_min_blocks); the searches of a width are also called
+# out of line by the kernels of wider roots (their narrow subproblems), so
+# each unit is capped at the smallest bound among its callers.
+MAXRREG = {"kc_enum_w1.cu": 64, "kc_enum_w2.cu": 64, "kc_enum_w4.cu": 128, "kc_enum_w8.cu": 128,
            "kc_enum_w16.cu": 128, "kc_enum_w32.cu": 128}
 
 

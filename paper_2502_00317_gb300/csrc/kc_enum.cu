@@ -70,6 +70,9 @@ struct TierPlan {
   uint32_t depth = 0;          // stack depth of the per-warp states
   uint32_t sstride = 0;        // shared-memory bytes per warp
   uint32_t coff = 0;           // offset of the narrow branch state in them
+  uint32_t soff_stats = 0;     // offset of the per-root counters
+  uint32_t soff_cache = 0;     // offset of the memo cache
+  uint32_t mcache = 0;         // memo cache entries per warp
   uint32_t memo_cap = 0;       // entries per warp (0: no memo)
   uint64_t memo_bytes = 0;
   uint32_t larena_bytes = 0;   // listing with the memo: arena bytes per warp
@@ -105,7 +108,12 @@ static int plan_tier(kc_ctx* ctx, int t, int mode, uint32_t nroots, bool split, 
   tp->mode = mode;
   tp->nroots = nroots;
   tp->depth = depth;
-  tp->sstride = (uint32_t)warp_smem_bytes(W, (int)depth);
+  // the memo cache in shared memory: 128 entries up to 2 words, 64 at 4, 32 beyond (so
+  // that it costs no resident block)
+  tp->mcache = (mode == 2 || mode == 3) ? (W <= 2 ? 128u : (W <= 4 ? 64u : 32u)) : 0u;
+  tp->soff_stats = (uint32_t)warp_smem_bytes(W, (int)depth) - 64u;
+  tp->soff_cache = (uint32_t)warp_smem_bytes(W, (int)depth);
+  tp->sstride = tp->soff_cache + (uint32_t)memo_cache_bytes(W, tp->mcache);
   tp->coff = in_smem ? (uint32_t)wbytes : 0u;
   tier_kernels(t, mode, &tp->fn, &tp->fn_tasks);
   if (nroots == 0) return KC_OK;
@@ -219,6 +227,9 @@ static int launch_tiers(kc_ctx* ctx, const EnumKArgs& args, const uint32_t* hcnt
     EnumKArgs x = args;
     x.sstride = tp.sstride;
     x.coff = tp.coff;
+    x.soff_stats = tp.soff_stats;
+    x.soff_cache = tp.soff_cache;
+    x.mcache = tp.mcache;
     x.roots = troots[t];
     x.roots_q = troots_q ? troots_q[t] : nullptr;
     x.nroots = tp.nroots;
@@ -625,6 +636,9 @@ int static_tier(int t, int num_sms, const EnumKArgs& x, cudaStream_t s) {
   EnumKArgs y = x;
   y.sstride = (uint32_t)sstride;
   y.coff = (uint32_t)warp_state_stride(W, (int)x.depth);
+  y.soff_stats = (uint32_t)sstride - 64u;
+  y.soff_cache = (uint32_t)sstride;
+  y.mcache = 0;
   void* kargs[] = {&y};
   KC_CUDA(cudaLaunchKernel(fe, dim3((unsigned)blocks), dim3(wpb * 32), kargs, smem, s));
   return KC_OK;

@@ -63,7 +63,10 @@ typedef struct kc_opts {
   uint32_t decomposition;  /* how roots become GPU work items (Sec. VII-D): KC_NODE_PARALLEL (0, default):
                               one warp per root, heavy roots split as above; KC_EDGE_PARALLEL: every
                               root's first-level branches (u, v) are separate tasks, for any k >= 3 */
-  uint32_t reserved0;
+  uint32_t autotune;       /* 1: kc_count and kc_count_batched pick their launch settings (see kc_tune) per
+                              class of input, probing once per class and caching the choice */
+  const char* tune_cache;  /* file that keeps the tuned choices across processes (NULL: the environment
+                              variable KC_TUNE_CACHE, else memory only); read at kc_create, appended to */
 } kc_opts;
 
 #define KC_NODE_PARALLEL 0u
@@ -345,6 +348,32 @@ int kc_serve_stats_get(kc_ctx* ctx, kc_serve_stats* out);
 /* Stop serving: requests not yet taken by a lane complete with status
  * KC_E_BUSY, running batches finish, the lanes are released. */
 int kc_serve_stop(kc_ctx* ctx);
+
+/* ------------------------------------------------------------ autotuning
+ * Launch settings with no counterpart in the paper: warps per block of the
+ * narrow (up to 4 words) and wide width tiers, the heavy-root split
+ * threshold, and the memo budget.  kc_tune times the batched count of the
+ * given queries (graphs[i], ks[i]) under candidate settings -- the split
+ * threshold first, then each warps-per-block choice, then the memo budget,
+ * keeping each change that is faster -- and applies the fastest to the
+ * context (every later call uses it).  The result is the same count under
+ * every setting; only the time differs.  *out (may be NULL) reports the
+ * choice, the probe times, and the class key under which the choice is
+ * cached (graph sizes, width tiers and k of the queries, and the GPU).
+ * Errors: those of kc_count_batched.  Synchronises the context's stream. */
+typedef struct kc_tune_result {
+  uint32_t split_threshold;  /* chosen (kc_opts encoding: 0xFFFFFFFF never) */
+  uint32_t warps_small;      /* warps per block, tiers of 1-4 words */
+  uint32_t warps_large;      /* warps per block, tiers of 8-32 words */
+  uint32_t probes;           /* timed batched counts run */
+  uint64_t memo_bytes;       /* chosen memo budget */
+  float ms_default;          /* the probe under the default settings */
+  float ms_tuned;            /* the probe under the chosen settings */
+  uint32_t cached;           /* 1: taken from the cache, no probe run */
+  char key[116];             /* class key, NUL-terminated */
+} kc_tune_result;
+
+int kc_tune(kc_ctx* ctx, const kc_graph* graphs, const uint32_t* ks, uint32_t nq, kc_tune_result* out);
 
 /* Telemetry of the last count/list call, and of the last upload. */
 int kc_last_stats(kc_ctx* ctx, kc_stats* out);

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkc.so")
-SOURCES = ["kc_api.cu", "kc_prep.cu", "kc_enum.cu", "kc_serve.cu", "kc_enum_w1.cu", "kc_enum_w2.cu", "kc_enum_w4.cu",
+SOURCES = ["kc_api.cu", "kc_prep.cu", "kc_enum.cu", "kc_serve.cu", "kc_tune.cu", "kc_enum_w1.cu", "kc_enum_w2.cu", "kc_enum_w4.cu",
            "kc_enum_w8.cu", "kc_enum_w16.cu", "kc_enum_w32.cu"]
 PEAK_SOURCE = "kc_peak.cu"  # separate library: the benchmark's integer-pipe peak
 PEAK_LIB = os.path.join(BUILD, "libkc_peak.so")

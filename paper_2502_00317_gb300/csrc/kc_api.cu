@@ -120,6 +120,9 @@ int kc_create(kc_ctx** out, int device, const kc_opts* opts) {
   if (e != cudaSuccess) return fail(e, "cudaGetDeviceProperties");
   ctx->num_sms = prop.multiProcessorCount;
   ctx->smem_optin = prop.sharedMemPerBlockOptin;
+  for (const char* c = prop.name; *c; c++) ctx->gpu_name.push_back(*c == ' ' ? '_' : *c);
+  tune_load(ctx);
+  ctx->opts.tune_cache = nullptr;  // the caller's string need not outlive kc_create
   if ((e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return fail(e, "cudaStreamCreate");
   for (int t = 0; t < kTiers; t++) {
@@ -287,6 +290,10 @@ int kc_count(kc_ctx* ctx, kc_graph h, uint32_t k, uint64_t* count, void* stream)
     *count = it->second.m;
     return KC_OK;
   }
+  if (ctx->opts.autotune && k <= KC_MAX_K && (uint64_t)k - 1 <= it->second.max_out) {
+    KC_CUDA(cudaSetDevice(ctx->device));
+    KC_TRY(tune_for_graph(ctx, it->second, k, pick_stream(ctx, stream)));
+  }
   return enum_common(ctx, h, k, 0, 0, it->second.n, nullptr, 0, nullptr, count, nullptr, stream);
 }
 
@@ -328,6 +335,15 @@ int kc_count_batched(kc_ctx* ctx, const kc_graph* graphs, const uint32_t* ks, ui
   }
   KC_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = pick_stream(ctx, stream);
+  if (ctx->opts.autotune) {
+    uint64_t tiers[kTiers] = {0};
+    for (uint32_t i = 0; i < nq; i++) {
+      if (!q[i].n) continue;
+      const DevGraph& g = ctx->graphs.find(graphs[i])->second;
+      for (int t = 0; t < kTiers; t++) tiers[t] += g.tier_roots[t];
+    }
+    KC_TRY(tune_for_batch(ctx, q.data(), nq, tiers, s, nullptr));
+  }
   ctx->last = kc_stats{};
   std::vector<uint64_t> got(std::max<uint32_t>(nq, 1), 0);
   KC_TRY(run_batch(ctx, q.data(), nq, ctx->opts.no_memo == 0, ctx->opts.no_prune == 0, got.data(), s));

@@ -71,8 +71,6 @@ struct TierPlan {
   uint32_t sstride = 0;        // shared-memory bytes per warp
   uint32_t coff = 0;           // offset of the narrow branch state in them
   uint32_t soff_stats = 0;     // offset of the per-root counters
-  uint32_t soff_cache = 0;     // offset of the memo cache
-  uint32_t mcache = 0;         // memo cache entries per warp
   uint32_t memo_cap = 0;       // entries per warp (0: no memo)
   uint64_t memo_bytes = 0;
   uint32_t larena_bytes = 0;   // listing with the memo: arena bytes per warp
@@ -108,16 +106,14 @@ static int plan_tier(kc_ctx* ctx, int t, int mode, uint32_t nroots, bool split, 
   tp->mode = mode;
   tp->nroots = nroots;
   tp->depth = depth;
-  // the memo cache in shared memory: 128 entries up to 2 words, 64 at 4, 32 beyond (so
-  // that it costs no resident block)
-  tp->mcache = (mode == 2 || mode == 3) ? (W <= 2 ? 128u : (W <= 4 ? 64u : 32u)) : 0u;
-  tp->soff_stats = (uint32_t)warp_smem_bytes(W, (int)depth) - 64u;
-  tp->soff_cache = (uint32_t)warp_smem_bytes(W, (int)depth);
-  tp->sstride = tp->soff_cache + (uint32_t)memo_cache_bytes(W, tp->mcache);
+  tp->sstride = (uint32_t)warp_smem_bytes(W, (int)depth);
+  tp->soff_stats = tp->sstride - 64u;
   tp->coff = in_smem ? (uint32_t)wbytes : 0u;
   tier_kernels(t, mode, &tp->fn, &tp->fn_tasks);
   if (nroots == 0) return KC_OK;
-  tp->warps_per_block = W <= 4 ? 8 : 4;
+  // warps per block: 8 and 4 by default, or the autotuner's choice (within the kernels' bounds)
+  tp->warps_per_block = W <= 4 ? (ctx->tuning.wpb_small ? (int)ctx->tuning.wpb_small : 8)
+                               : (ctx->tuning.wpb_large ? (int)ctx->tuning.wpb_large : 4);
   tp->smem = (size_t)tp->sstride * tp->warps_per_block;
   if (tp->smem > 48 * 1024) {
     KC_CUDA(cudaFuncSetAttribute(tp->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp->smem));
@@ -148,7 +144,8 @@ static int plan_tier(kc_ctx* ctx, int t, int mode, uint32_t nroots, bool split, 
     // a window of 32 slots is the smallest table, and a tier that cannot get one counts without
     uint64_t warps = blocks * tp->warps_per_block;
     uint32_t cap = 1u << 12;
-    uint64_t budget = ctx->opts.memo_bytes ? ctx->opts.memo_bytes : (1ull << 30);
+    uint64_t budget = ctx->tuning.memo_bytes ? ctx->tuning.memo_bytes
+                      : (ctx->opts.memo_bytes ? ctx->opts.memo_bytes : (1ull << 30));
     uint64_t per_entry = 4 + 4ull * W + 8;
     while (cap > 32 && warps * cap * per_entry > budget / kTiers) cap >>= 1;
     if (warps * cap * per_entry > budget / kTiers) {
@@ -191,9 +188,9 @@ constexpr uint32_t kDefaultSplitWedges = 16384;
 static int launch_tiers(kc_ctx* ctx, const EnumKArgs& args, const uint32_t* hcnt, uint32_t* const* troots,
                         uint32_t* const* troots_q, int mode, bool split_ok, cudaStream_t s, uint32_t* launches,
                         uint32_t* enum_launches) {
+  const uint32_t split_opt = ctx->tuning.split ? ctx->tuning.split : ctx->opts.split_threshold;
   const uint32_t split_wedges =
-      ctx->opts.split_threshold == 0 ? kDefaultSplitWedges
-      : (ctx->opts.split_threshold == 0xFFFFFFFFu ? 0u : ctx->opts.split_threshold);
+      split_opt == 0 ? kDefaultSplitWedges : (split_opt == 0xFFFFFFFFu ? 0u : split_opt);
   // the split path needs at least two levels below the first branch (k >= 5)
   // EdgeParallel decomposition (kc_opts.decomposition): every root of every
   // tier is split into its first-level branches, for any k >= 3
@@ -228,8 +225,6 @@ static int launch_tiers(kc_ctx* ctx, const EnumKArgs& args, const uint32_t* hcnt
     x.sstride = tp.sstride;
     x.coff = tp.coff;
     x.soff_stats = tp.soff_stats;
-    x.soff_cache = tp.soff_cache;
-    x.mcache = tp.mcache;
     x.roots = troots[t];
     x.roots_q = troots_q ? troots_q[t] : nullptr;
     x.nroots = tp.nroots;
@@ -637,8 +632,6 @@ int static_tier(int t, int num_sms, const EnumKArgs& x, cudaStream_t s) {
   y.sstride = (uint32_t)sstride;
   y.coff = (uint32_t)warp_state_stride(W, (int)x.depth);
   y.soff_stats = (uint32_t)sstride - 64u;
-  y.soff_cache = (uint32_t)sstride;
-  y.mcache = 0;
   void* kargs[] = {&y};
   KC_CUDA(cudaLaunchKernel(fe, dim3((unsigned)blocks), dim3(wpb * 32), kargs, smem, s));
   return KC_OK;

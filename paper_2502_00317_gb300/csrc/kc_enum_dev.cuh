@@ -81,14 +81,7 @@ struct EnumKArgs {
   uint32_t sstride;             // shared-memory bytes per warp
   uint32_t coff;                // offset of the narrow branch state in the warp's shared memory
   uint32_t soff_stats;          // offset of the warp's per-root counters
-  uint32_t soff_cache;          // offset of the warp's memo cache
-  uint32_t mcache;              // memo cache entries per warp (power of two; 0: none)
 };
-
-// Shared-memory bytes of a memo cache of `entries` at width W (values, tags, keys).
-__host__ __device__ constexpr size_t memo_cache_bytes(int W, uint32_t entries) {
-  return ((size_t)entries * (8 + 4 + 4 * (size_t)W) + 15) & ~(size_t)15;
-}
 
 // Bytes of one warp's working state at width W with stacks of depth D (the
 // layout of WarpState::carve; D = k + 1 covers every depth of a k-clique search).
@@ -220,13 +213,6 @@ struct Memo {
   uint8_t* lar;      // listing with the trie: this warp's arena of stored clique lists
   uint32_t lcap;     // its bytes
   uint32_t* ltop;    // bytes the current root has used (lives in the kernel)
-  // a direct-mapped cache of recent entries in the warp's shared memory, in
-  // front of the table (0 entries: none); most hits are entries the warp
-  // stored a moment before (a sibling frame's prefix)
-  uint32_t* ctags;
-  uint32_t* ckeys;
-  unsigned long long* cvals;
-  uint32_t ccap;
 };
 
 // MODE 1 lists plainly, MODE 3 lists with the trie (both report cliques).
@@ -269,41 +255,13 @@ __device__ __forceinline__ int memo_probe(const Memo& m, const uint32_t (&key)[W
   return bm ? (int)((h + __ffs(bm) - 1) & (m.cap - 1)) : -1;
 }
 
-// Puts (key, l) -> val in the cache slot of hash h (the whole warp).
-template <int W>
-__device__ __forceinline__ void memo_cache_put(const Memo& m, const uint32_t (&key)[W], uint32_t l, uint32_t h,
-                                               unsigned long long val) {
-  if (!m.ccap) return;
-  const uint32_t lane = lane_id();
-  const uint32_t cs = h & (m.ccap - 1);
-  __syncwarp();
-  if (lane < W) m.ckeys[cs * W + lane] = word_at<W>(key, lane);
-  if (lane == 0) {
-    m.cvals[cs] = val;
-    m.ctags[cs] = m.tagbase | l;
-  }
-  __syncwarp();
-}
-
 template <int W>
 __device__ __forceinline__ bool memo_find(const Memo& m, const uint32_t (&key)[W], uint32_t l,
                                           unsigned long long* val) {
-  const uint32_t h = memo_hash<W>(key, l);
-  if (m.ccap) {
-    const uint32_t cs = h & (m.ccap - 1);
-    bool hit = m.ctags[cs] == (m.tagbase | l);
-#pragma unroll
-    for (int w = 0; w < W; w++) hit = hit && m.ckeys[cs * W + w] == key[w];
-    if (hit) {
-      *val = m.cvals[cs];
-      return true;
-    }
-  }
   int fs;
-  int s = memo_probe<W>(m, key, l, h, &fs);
+  int s = memo_probe<W>(m, key, l, memo_hash<W>(key, l), &fs);
   if (s < 0) return false;
   *val = m.vals[s];
-  memo_cache_put<W>(m, key, l, h, *val);
   return true;
 }
 
@@ -311,7 +269,6 @@ __device__ __forceinline__ bool memo_find(const Memo& m, const uint32_t (&key)[W
 template <int W>
 __device__ __forceinline__ int memo_store(const Memo& m, const uint32_t (&key)[W], uint32_t l, unsigned long long val) {
   const uint32_t h = memo_hash<W>(key, l);
-  memo_cache_put<W>(m, key, l, h, val);
   int fs;
   int s = memo_probe<W>(m, key, l, h, &fs);
   if (s < 0) s = fs;
@@ -330,7 +287,6 @@ __device__ __forceinline__ int memo_store(const Memo& m, const uint32_t (&key)[W
 __device__ __forceinline__ void next_epoch(Memo& memo, uint32_t* epoch) {
   if (++*epoch >= (1u << 25)) {
     for (uint32_t i = lane_id(); i < memo.cap; i += 32) memo.tags[i] = 0u;
-    for (uint32_t i = lane_id(); i < memo.ccap; i += 32) memo.ctags[i] = 0u;
     __syncwarp();
     *epoch = 1;
   }
@@ -1684,19 +1640,10 @@ __device__ __forceinline__ void carve_state(WarpState<W>& st, const EnumKArgs& a
 // the first half serves the root's index space, the second the narrow
 // subproblems (each of which starts its own epoch there).
 template <int W>
-__device__ __forceinline__ void warp_memo(const EnumKArgs& a, uint8_t* smem, Memo* m, Memo* m2) {
+__device__ __forceinline__ void warp_memo(const EnumKArgs& a, Memo* m, Memo* m2) {
   const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   *m = Memo{};
   *m2 = Memo{};
-  if (a.mcache && a.memo_cap) {
-    uint8_t* c = smem + (size_t)(threadIdx.x >> 5) * a.sstride + a.soff_cache;
-    m->cvals = (unsigned long long*)c;
-    m->ctags = (uint32_t*)(c + (size_t)a.mcache * 8);
-    m->ckeys = m->ctags + a.mcache;
-    m->ccap = a.mcache;
-    for (uint32_t i = lane_id(); i < a.mcache; i += 32) m->ctags[i] = 0u;
-    __syncwarp();
-  }
   if (a.larena) {
     m->lar = a.larena + gwarp * a.larena_bytes;
     m->lcap = a.larena_bytes;
@@ -1855,7 +1802,7 @@ __global__ void __launch_bounds__(kc_block_threads(W), kc_min_blocks(W)) k_enum(
   carve_state<W>(st, a, smem);
   Acc acc;
   Memo memo, memo2;
-  warp_memo<W>(a, smem, &memo, &memo2);
+  warp_memo<W>(a, &memo, &memo2);
   uint32_t ltop = 0;
   memo.ltop = &ltop;
   uint32_t epoch = 0, epoch2 = 0;
@@ -1895,7 +1842,7 @@ __global__ void __launch_bounds__(kc_block_threads(W), kc_min_blocks(W)) k_tasks
   uint32_t need = a.k - 1;
   Acc acc;
   Memo memo, memo2;
-  warp_memo<W>(a, smem, &memo, &memo2);
+  warp_memo<W>(a, &memo, &memo2);
   uint32_t ltop = 0;
   memo.ltop = &ltop;
   uint32_t epoch = 1u << 24, epoch2 = 1u << 24;  // above every epoch of phase 1

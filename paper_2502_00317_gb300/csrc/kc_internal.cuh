@@ -117,6 +117,15 @@ struct Scratch {
 
 struct Server;  // the serving loop (kc_serve.cu)
 
+// Launch settings chosen by the autotuner (kc_tune.cu); a zero field keeps
+// the default.
+struct Tuning {
+  uint32_t split = 0;       // kc_opts.split_threshold encoding
+  uint32_t wpb_small = 0;   // warps per block, tiers of 1-4 words (default 8)
+  uint32_t wpb_large = 0;   // warps per block, tiers of 8-32 words (default 4)
+  uint64_t memo_bytes = 0;  // memo budget (default kc_opts.memo_bytes, else 1 GiB)
+};
+
 }  // namespace kc
 
 struct kc_ctx {
@@ -145,6 +154,10 @@ struct kc_ctx {
   kc_upload_stats last_up{};
   std::string last_error;
   kc::Server* server = nullptr;           // kc_serve_* state, if serving was ever started
+  kc::Tuning tuning;                      // launch settings in force (autotuner)
+  std::unordered_map<std::string, kc::Tuning> tune_table;  // tuned settings by class key
+  std::string tune_path;                  // file of tuned settings ("" : memory only)
+  std::string gpu_name;
 };
 
 namespace kc {
@@ -239,5 +252,13 @@ struct BatchQuery {
 };
 int run_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, bool memo, bool prune, uint64_t* counts,
               cudaStream_t s, uint64_t* checksums = nullptr);
+
+// Autotuning (kc_tune.cu): load the cache file (kc_create); apply the tuned
+// settings of a batch's class, probing first when the class is new
+// (tier_roots: the batch's roots per width tier, summed over its graphs).
+void tune_load(kc_ctx* ctx);
+int tune_for_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, const uint64_t* tier_roots, cudaStream_t s,
+                   kc_tune_result* out);
+int tune_for_graph(kc_ctx* ctx, const DevGraph& g, uint32_t k, cudaStream_t s);
 
 }  // namespace kc

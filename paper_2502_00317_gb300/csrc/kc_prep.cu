@@ -860,6 +860,8 @@ int prep_graph(kc_ctx* ctx, uint32_t n, const uint64_t* rowptr_in, const uint32_
   KC_CUDA(cudaEventRecord(ev[3], s));
   // ---- orient
   uint32_t* outdeg = frontier;  // reuse (peel is done with it)
+  // the tier counts (canonicalisation used the same words for its longest row)
+  KC_CUDA(cudaMemsetAsync(d_small + 8, 0, (kTiers + 1) * sizeof(uint32_t), s));
   if (n > 0) {
     k_orient_count<<<wgrid, 256, 0, s>>>(rowptr, col, n, g->rank, outdeg, d_maxout, d_small + 8);
     KC_CUDA(cudaGetLastError());

@@ -40,6 +40,7 @@ EXPORTS = (
     "kc_count", "kc_list", "kc_list_range", "kc_last_stats", "kc_last_upload_stats", "kc_strerror",
     "kc_last_error", "kc_count_dag_noalloc", "kc_count_batched", "kc_serve_start", "kc_serve_submit",
     "kc_serve_submit_csr", "kc_serve_poll", "kc_serve_wait", "kc_serve_stats_get", "kc_serve_stop",
+    "kc_tune",
 )
 
 KC_SERVE_COUNT = 0
@@ -65,7 +66,22 @@ class kc_opts(ctypes.Structure):
         ("memo_bytes", ctypes.c_uint64),
         ("spin_limit", ctypes.c_uint64),
         ("decomposition", ctypes.c_uint32),
-        ("reserved0", ctypes.c_uint32),
+        ("autotune", ctypes.c_uint32),
+        ("tune_cache", ctypes.c_char_p),
+    ]
+
+
+class kc_tune_result(ctypes.Structure):
+    _fields_ = [
+        ("split_threshold", ctypes.c_uint32),
+        ("warps_small", ctypes.c_uint32),
+        ("warps_large", ctypes.c_uint32),
+        ("probes", ctypes.c_uint32),
+        ("memo_bytes", ctypes.c_uint64),
+        ("ms_default", ctypes.c_float),
+        ("ms_tuned", ctypes.c_float),
+        ("cached", ctypes.c_uint32),
+        ("key", ctypes.c_char * 116),
     ]
 
 
@@ -196,6 +212,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kc_serve_wait": (i32, [P, u64, ctypes.c_int64, ctypes.POINTER(kc_serve_result)]),
         "kc_serve_stats_get": (i32, [P, ctypes.POINTER(kc_serve_stats)]),
         "kc_serve_stop": (i32, [P]),
+        "kc_tune": (i32, [P, P, P, u32, ctypes.POINTER(kc_tune_result)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -232,9 +249,10 @@ def kc_strerror(status: int) -> str:
 
 
 def kc_create(device: int = 0, no_memo: bool = False, no_prune: bool = False, memo_bytes: int = 0,
-              spin_limit: int = 0, split_threshold: int = 0, decomposition: int = 0) -> int:
+              spin_limit: int = 0, split_threshold: int = 0, decomposition: int = 0, autotune: bool = False,
+              tune_cache: str | None = None) -> int:
     o = kc_opts(ctypes.sizeof(kc_opts), int(no_memo), int(no_prune), int(split_threshold), int(memo_bytes),
-                int(spin_limit), int(decomposition), 0)
+                int(spin_limit), int(decomposition), int(autotune), tune_cache.encode() if tune_cache else None)
     h = ctypes.c_void_p()
     _check(load().kc_create(ctypes.byref(h), int(device), ctypes.byref(o)), "kc_create")
     return h.value
@@ -322,6 +340,20 @@ def kc_count_batched(ctx: int, graphs, ks, stream=None) -> list[int]:
     _check(load().kc_count_batched(ctypes.c_void_p(ctx), _ptr(g), _ptr(k), int(g.size), _ptr(out), _stream(stream)),
            "kc_count_batched")
     return [int(x) for x in out[: g.size]]
+
+
+def kc_tune(ctx: int, graphs, ks) -> dict:
+    """Times the batched count of (graphs[i], ks[i]) under candidate launch
+    settings and applies the fastest to the context; returns the choice."""
+    g = np.ascontiguousarray(graphs, dtype=np.uint32)
+    k = np.ascontiguousarray(ks, dtype=np.uint32)
+    if g.shape != k.shape:
+        raise ValueError("graphs and ks differ in length")
+    r = kc_tune_result()
+    _check(load().kc_tune(ctypes.c_void_p(ctx), _ptr(g), _ptr(k), int(g.size), ctypes.byref(r)), "kc_tune")
+    d = _struct_dict(r)
+    d["key"] = r.key.decode()
+    return d
 
 
 def kc_serve_start(ctx: int, lanes: int = 0, max_batch: int = 0, mem_cap_bytes: int = 0) -> None:
@@ -434,6 +466,9 @@ class Context:
     def list_range(self, g: int, k: int, lo: int, hi: int, d_buf=None, cap: int = 0, stream=None,
                    allow_capacity: bool = False):
         return kc_list_range(self.h, g, k, lo, hi, d_buf, cap, stream, allow_capacity)
+
+    def tune(self, graphs, ks) -> dict:
+        return kc_tune(self.h, graphs, ks)
 
     def count_batched(self, graphs, ks, stream=None) -> list[int]:
         return kc_count_batched(self.h, graphs, ks, stream)

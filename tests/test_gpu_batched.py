@@ -79,3 +79,45 @@ def test_batched_errors():
             assert e.value.status == code
         assert c.count_batched([h, h], [3, 4]) == [20, 15]
         c.free(h)
+
+
+def test_autotuner_choice_is_cached_and_changes_no_count(tmp_path):
+    """kc_tune times the batch under candidate launch settings (warps per
+    block, split threshold, memo budget) and applies the fastest: counts are
+    unchanged.  With autotune on, the first batched call of a class probes
+    and appends its choice to the cache file; a new context that reads the
+    file uses the stored choice without probing (the file does not grow)."""
+    batch = gg.config_batched(seed=6, count=48, nmax=3000)
+    cache = tmp_path / "tune.txt"
+    with kc.Context(0) as c:
+        hs = [c.upload_host(g.n, g.rowptr, g.col) for g, _ in batch]
+        ks = [k for _, k in batch]
+        want = [c.count(h, k) for h, k in zip(hs, ks)]
+        r = c.tune(hs, ks)
+        assert r["probes"] >= 2 and r["ms_tuned"] <= r["ms_default"], r
+        assert r["warps_small"] in (4, 8) and r["warps_large"] in (2, 4), r
+        assert r["key"].startswith("NVIDIA") or "/" in r["key"], r
+        assert c.count_batched(hs, ks) == want
+        assert [c.count(h, k) for h, k in zip(hs, ks)] == want
+        for h in hs:
+            c.free(h)
+    with kc.Context(0, autotune=True, tune_cache=str(cache)) as c:
+        hs = [c.upload_host(g.n, g.rowptr, g.col) for g, _ in batch]
+        assert c.count_batched(hs, ks) == want
+        lines = cache.read_text().splitlines()
+        assert len(lines) == 1 and len(lines[0].split()) == 5, lines
+        for h in hs:
+            c.free(h)
+    with kc.Context(0, autotune=True, tune_cache=str(cache)) as c:
+        hs = [c.upload_host(g.n, g.rowptr, g.col) for g, _ in batch]
+        assert c.count_batched(hs, ks) == want
+        assert cache.read_text().splitlines() == lines  # taken from the file, no new probe
+        # a single graph in autotune mode: its class is probed once, on its dense core
+        g, k = gg.chung_lu_planted(n=20000, n_cliques=40, seed=1), 7
+        h = c.upload_host(g.n, g.rowptr, g.col)
+        assert c.count(h, k) == oracle.OracleGraph.from_graph(g).count(k)[0]
+        assert len(cache.read_text().splitlines()) == 2
+        assert c.count(h, k) == oracle.OracleGraph.from_graph(g).count(k)[0]
+        assert len(cache.read_text().splitlines()) == 2
+        for hh in hs + [h]:
+            c.free(hh)

@@ -1670,13 +1670,13 @@ __device__ __forceinline__ void warp_memo(const EnumKArgs& a, Memo* m, Memo* m2)
 // count or list.  Counts accumulate in acc.cnt (lane-partial).
 template <int W, int MODE>
 __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint32_t* epoch, Memo& memo2,
-                          uint32_t* epoch2, uint32_t u, Acc& acc) {
+                          uint32_t* epoch2, uint32_t u, Acc& acc, bool timed) {
   const uint32_t lane = lane_id();
   const uint32_t need = a.k - 1;
   const int d = (int)(a.orow[u + 1] - a.orow[u]);
-  const unsigned long long tb = global_ns();
+  const unsigned long long tb = timed ? global_ns() : 0ull;
   const bool kept = build_root<W>(st, a, u, d, acc);
-  if (lane == 0) st.stats[kWsBuildNs] += global_ns() - tb;
+  if (timed && lane == 0) st.stats[kWsBuildNs] += global_ns() - tb;
   if (!kept) return;
   uint32_t S0[W];
   all_bits<W>(d, S0);
@@ -1718,11 +1718,13 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
     const uint32_t thr = dense0 ? (a.split_wedges >> min(need - 4u, 12u)) : a.split_wedges;
     if (wg > thr && publish_root<W, MODE>(st, a, u, d, acc, d, dense0)) return;
   }
-  if (W >= 2 && (need >= 4 || (is_list(MODE) && need >= 2))) {
-    // the root frame of a wide root: one branch after another, from the
-    // largest vertex down (the order of the identifying strings, so that a
-    // dense branch resumes from its sibling's stored set), each searched in
-    // a narrow state where its candidate set allows
+  if (W >= 16 && (need >= 4 || (is_list(MODE) && need >= 2))) {
+    // the root frame of a wide root (16 or 32 words): one branch after
+    // another, from the largest vertex down (the order of the identifying
+    // strings, so that a dense branch resumes from its sibling's stored set),
+    // each searched in a narrow state where its candidate set allows.
+    // Narrower roots search from the root frame itself: at 2 to 8 words a
+    // branch's re-indexing costs about what it saves.
     if (lane < W) st.cand[lane] = word_at<W>(S0, lane);
     __syncwarp();
     const uint32_t* m1 = st.masks + need * W;
@@ -1812,17 +1814,20 @@ __global__ void __launch_bounds__(kc_block_threads(W), kc_min_blocks(W)) k_enum(
     qi = __shfl_sync(0xFFFFFFFFu, qi, 0);
     if (qi >= a.nroots) break;
     const uint32_t u = a.roots[qi];
-    const unsigned long long t0 = global_ns();
+    // one root in 16 of each warp is timed (the clock read is not free): the
+    // build's share of warp time is estimated on those
+    const bool timed = (qi & 15u) == 0;
+    const unsigned long long t0 = timed ? global_ns() : 0ull;
     if (a.bq) {
       const uint32_t q = a.roots_q[qi];
       EnumKArgs b = a;
       bind_query(b, a, q);
-      root_body<W, MODE>(st, b, memo, &epoch, memo2, &epoch2, u, acc);
+      root_body<W, MODE>(st, b, memo, &epoch, memo2, &epoch2, u, acc, timed);
       flush_query<MODE>(a, q, acc);
     } else {
-      root_body<W, MODE>(st, a, memo, &epoch, memo2, &epoch2, u, acc);
+      root_body<W, MODE>(st, a, memo, &epoch, memo2, &epoch2, u, acc, timed);
     }
-    if (lane == 0) st.stats[kWsBusyNs] += global_ns() - t0;
+    if (timed && lane == 0) st.stats[kWsBusyNs] += global_ns() - t0;
     acc.ops64 += acc.ops;
     acc.ops = 0;
     __syncwarp();
@@ -1856,7 +1861,8 @@ __global__ void __launch_bounds__(kc_block_threads(W), kc_min_blocks(W)) k_tasks
     if (lane == 0) t = atomicAdd(a.task_head, 1ull);
     t = __shfl_sync(0xFFFFFFFFu, t, 0);
     if (t >= ntasks) break;
-    const unsigned long long t0 = global_ns();
+    const bool timed = (t & 15ull) == 0;
+    const unsigned long long t0 = timed ? global_ns() : 0ull;
     const unsigned long long task = a.tasks[t];
     const unsigned long long off = task >> 32;
     const int v1 = (int)(task & 0xFFFFFFFFull);
@@ -1907,7 +1913,7 @@ __global__ void __launch_bounds__(kc_block_threads(W), kc_min_blocks(W)) k_tasks
     // the kernel's own arguments are read in place; only a batch binds a copy
     run_branch<W, MODE>(st, a.bq ? b : a, memo, memo2, &epoch2, u, d, v1, acc, dense);
     if (a.bq) flush_query<MODE>(a, b.query, acc);
-    if (lane == 0) st.stats[kWsBusyNs] += global_ns() - t0;
+    if (timed && lane == 0) st.stats[kWsBusyNs] += global_ns() - t0;
     acc.ops64 += acc.ops;
     acc.ops = 0;
     __syncwarp();

@@ -51,7 +51,7 @@ def _args():
                         "decomposition variants on configs 2 and 3")
     p.add_argument("--chunk", type=float, default=2 ** 29, help="rmat: about this many cliques in the listed chunk")
     p.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
-    p.add_argument("--duration", type=float, default=20.0, help="serve: seconds of arrivals")
+    p.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     p.add_argument("--count", type=int, default=4096, help="graphs in the batched workload")
     return p.parse_args()
 
@@ -522,16 +522,23 @@ def run_batched(a):
     def separate():
         return [ctx.count(h, k, stream) for h, k in zip(hs, ks)]
 
+    # the fixed default launch settings first, then the autotuner's choice for this batch
     for _ in range(a.warmup):
         ref = batched()
+    _, tfix = timed(batched, a.steps)
+    t1 = time.time()
+    tune = ctx.tune(hs, ks)
+    tune_s = time.time() - t1
+    for _ in range(a.warmup):
+        ref2 = batched()
     sampler = ClockSampler(local)
     sampler.start()
     got, tb = timed(batched, a.steps)
     clocks = sampler.stop()
     st = ctx.stats()
     alone, tsep = timed(separate, max(1, min(a.steps, 2)))
-    assert got == ref == alone, "batched counts differ from per-graph counts"
-    ms, ms_sep = statistics.mean(tb), statistics.mean(tsep)
+    assert got == ref == ref2 == alone, "batched counts differ from per-graph counts"
+    ms, ms_sep, ms_fix = statistics.mean(tb), statistics.mean(tsep), statistics.mean(tfix)
     line = {
         "metric": "graphs/s (batched exact k-clique counts)", "value": len(batch) / (ms / 1e3), "unit": "graphs/s",
         "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -541,6 +548,13 @@ def run_batched(a):
                    "cliques": int(sum(got)), "l2": "flushed between timed steps", "resident": "CSRs uploaded once"},
         "per_graph_launches": {"value": len(batch) / (ms_sep / 1e3), "unit": "graphs/s", "ms_per_step": ms_sep},
         "speedup_vs_per_graph": ms_sep / ms,
+        "autotune": {"choice": {kk: tune[kk] for kk in ("split_threshold", "warps_small", "warps_large",
+                                                         "memo_bytes")},
+                     "class_key": tune["key"], "probes": tune["probes"], "tuning_s": tune_s,
+                     "probe_ms_default": tune["ms_default"], "probe_ms_tuned": tune["ms_tuned"],
+                     "fixed_settings": {"value": len(batch) / (ms_fix / 1e3), "unit": "graphs/s",
+                                        "ms_per_step": ms_fix},
+                     "speedup_vs_fixed": ms_fix / ms},
         "upload_s_all": upload_s,
         "gpu_launches": st["total_launches"] * a.steps,
         "clocks": clocks,
@@ -598,7 +612,9 @@ def run_serve(a):
     assert [r["count"] for r in res] == [r["count"] for r in base], "served counts depend on the mix"
     line = {
         "metric": "serve p50/p99 latency ms and throughput (req/s)", "value": st["req_per_s"], "unit": "req/s",
-        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "n_gpus": ws, "steps": 1, "warmup": 1,
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+        "p50_enumerated_ms": st["p50_enum_ms"], "p99_enumerated_ms": st["p99_enum_ms"],
+        "enumerated_requests": sum(1 for r in res if r["enumerated"]), "n_gpus": ws, "steps": 1, "warmup": 1,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64 (exact integer)",
         "data": "synthetic (seeded generator)",
         "config": {"workload": f"serve_poisson_{a.rate:g}rps_{a.duration:g}s_config4_pool{len(hs)}_k4-8",
@@ -606,6 +622,7 @@ def run_serve(a):
                    "resident": "CSRs uploaded once"},
         "serve": st,
         "one_request_per_launch": {"req_per_s": bst["req_per_s"], "p50_ms": bst["p50_ms"], "p99_ms": bst["p99_ms"],
+                                   "p50_enumerated_ms": bst["p50_enum_ms"], "p99_enumerated_ms": bst["p99_enum_ms"],
                                    "note": "same arrivals, one lane, batches of one request"},
         "clocks": clocks,
     }

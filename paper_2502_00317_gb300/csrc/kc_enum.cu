@@ -72,6 +72,7 @@ struct TierPlan {
   uint32_t coff = 0;           // offset of the narrow branch state in them
   uint32_t soff_stats = 0;     // offset of the per-root counters
   uint32_t memo_cap = 0;       // entries per warp (0: no memo)
+  uint32_t memo_cap2 = 0;      // and per warp for its narrow subproblems
   uint64_t memo_bytes = 0;
   uint32_t larena_bytes = 0;   // listing with the memo: arena bytes per warp
   bool split = false;          // heavy roots of this tier go to the split path
@@ -147,8 +148,10 @@ static int plan_tier(kc_ctx* ctx, int t, int mode, uint32_t nroots, bool split, 
     uint64_t budget = ctx->tuning.memo_bytes ? ctx->tuning.memo_bytes
                       : (ctx->opts.memo_bytes ? ctx->opts.memo_bytes : (1ull << 30));
     uint64_t per_entry = 4 + 4ull * W + 8;
-    while (cap > 32 && warps * cap * per_entry > budget / kTiers) cap >>= 1;
-    if (warps * cap * per_entry > budget / kTiers) {
+    // narrow subproblems get a table of their own, a quarter of the root's
+    auto cap2_of = [&](uint32_t c) { return compact_width(W) ? std::max<uint32_t>(32, c / 4) : 0u; };
+    while (cap > 32 && warps * (cap + cap2_of(cap)) * per_entry > budget / kTiers) cap >>= 1;
+    if (warps * (cap + cap2_of(cap)) * per_entry > budget / kTiers) {
       tp->mode = mode == 3 ? 1 : 0;
       tier_kernels(t, tp->mode, &tp->fn, &tp->fn_tasks);
       if (tp->smem > 48 * 1024) {
@@ -157,7 +160,8 @@ static int plan_tier(kc_ctx* ctx, int t, int mode, uint32_t nroots, bool split, 
       }
     } else {
       tp->memo_cap = cap;
-      tp->memo_bytes = warps * cap * per_entry;
+      tp->memo_cap2 = cap2_of(cap);
+      tp->memo_bytes = warps * (cap + tp->memo_cap2) * per_entry;
       if (mode == 3) {
         // the stored clique lists: up to four times the memo budget over the
         // tiers, 4 KiB to 256 KiB per warp
@@ -236,11 +240,13 @@ static int launch_tiers(kc_ctx* ctx, const EnumKArgs& args, const uint32_t* hcnt
     if (tp.memo_cap) {
       uint64_t warps = tp.blocks * tp.warps_per_block;
       uint8_t* mb = (uint8_t*)base + moff[t];
+      const uint64_t slots = warps * (uint64_t)(tp.memo_cap + tp.memo_cap2);
       x.memo_vals = (unsigned long long*)mb;
-      x.memo_tags = (uint32_t*)(mb + warps * tp.memo_cap * 8);
-      x.memo_keys = (uint32_t*)(mb + warps * tp.memo_cap * 12);
+      x.memo_tags = (uint32_t*)(mb + slots * 8);
+      x.memo_keys = (uint32_t*)(mb + slots * 12);
       x.memo_cap = tp.memo_cap;
-      KC_CUDA(cudaMemsetAsync(x.memo_tags, 0, warps * tp.memo_cap * 4, ts));
+      x.memo_cap2 = tp.memo_cap2;
+      KC_CUDA(cudaMemsetAsync(x.memo_tags, 0, slots * 4, ts));
     }
     if (tp.larena_bytes) {
       x.larena = (uint8_t*)base + loff[t];

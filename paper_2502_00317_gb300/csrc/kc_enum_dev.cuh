@@ -56,6 +56,7 @@ struct EnumKArgs {
   uint32_t* memo_keys;
   unsigned long long* memo_vals;
   uint32_t memo_cap;          // entries per warp (power of two)
+  uint32_t memo_cap2;         // entries per warp for its narrow subproblems (after those; 0: none)
   uint8_t* larena;            // listing with the trie: per-warp arenas of stored l-clique lists
   uint32_t larena_bytes;      // bytes per warp
   uint32_t* status;
@@ -1636,9 +1637,9 @@ __device__ __forceinline__ void carve_state(WarpState<W>& st, const EnumKArgs& a
   __syncwarp();
 }
 
-// This warp's memo tables.  With a narrow branch state the table is halved:
-// the first half serves the root's index space, the second the narrow
-// subproblems (each of which starts its own epoch there).
+// This warp's memo tables: the root's index space, then (where the width has
+// a narrow branch state) a quarter-size table for the narrow subproblems,
+// each of which starts its own epoch there.
 template <int W>
 __device__ __forceinline__ void warp_memo(const EnumKArgs& a, Memo* m, Memo* m2) {
   const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1649,20 +1650,18 @@ __device__ __forceinline__ void warp_memo(const EnumKArgs& a, Memo* m, Memo* m2)
     m->lcap = a.larena_bytes;
   }
   if (!a.memo_cap) return;
-  m->tags = a.memo_tags + gwarp * a.memo_cap;
-  m->keys = a.memo_keys + gwarp * a.memo_cap * W;
-  m->vals = a.memo_vals + gwarp * a.memo_cap;
+  const uint64_t stride = (uint64_t)a.memo_cap + a.memo_cap2;
+  m->tags = a.memo_tags + gwarp * stride;
+  m->keys = a.memo_keys + gwarp * stride * W;
+  m->vals = a.memo_vals + gwarp * stride;
   m->cap = a.memo_cap;
-  if (compact_width(W) && a.memo_cap >= 64) {
-    const uint32_t h = a.memo_cap / 2;
-    m->cap = h;
-    m2->tags = m->tags + h;
-    m2->keys = m->keys + (size_t)h * W;  // the narrow keys (width <= W/2) fit in the same stride
-    m2->vals = m->vals + h;
-    m2->cap = h;
+  if (a.memo_cap2) {
+    m2->tags = m->tags + a.memo_cap;
+    m2->keys = m->keys + (size_t)a.memo_cap * W;  // the narrow keys (width <= W/2) fit in the same stride
+    m2->vals = m->vals + a.memo_cap;
+    m2->cap = a.memo_cap2;
   }
 }
-
 
 // Phase 1: one warp per root, roots taken from the tier's list.
 // MODE 0: count (plain), 1: list, 2: count with memo, 3: list with memo.

@@ -67,6 +67,8 @@ typedef struct kc_opts {
                               class of input, probing once per class and caching the choice */
   const char* tune_cache;  /* file that keeps the tuned choices across processes (NULL: the environment
                               variable KC_TUNE_CACHE, else memory only); read at kc_create, appended to */
+  uint32_t no_plex;        /* 1: never count a 2-plex subgraph by its closed form (the 2-plex early
+                              termination of Sec. VII-A); counting only, listing never uses it */
 } kc_opts;
 
 #define KC_NODE_PARALLEL 0u
@@ -104,6 +106,7 @@ typedef struct kc_stats {
   uint64_t warp_ns_build;  /* summed over warps: nanoseconds spent building root bit-matrices (a5) */
   uint64_t warp_ns_busy;   /* summed over warps: nanoseconds spent on roots and tasks in all */
   uint64_t memo_peak;      /* most trie entries stored for one root (the size the paper bounds by tau) */
+  uint64_t plex_frames;    /* frames counted by the 2-plex closed form (Sec. VII-A) instead of a search */
 } kc_stats;
 
 /* Per-stage device times of the last kc_upload (CUDA events). */

@@ -143,6 +143,20 @@ int kc_create(kc_ctx** out, int device, const kc_opts* opts) {
   if ((e = cudaMallocHost(&ctx->h_acc, kAccSlots * sizeof(unsigned long long))) != cudaSuccess)
     return fail(e, "cudaMallocHost");
   cudaMemset(ctx->d_status, 0, 64);
+  {
+    // Pascal's triangle mod 2^64 (unsigned wrap-around is exact modular arithmetic)
+    const size_t rows = KC_MAX_OUTDEG + 1, cols = KC_MAX_K + 1;
+    std::vector<unsigned long long> tab(rows * cols, 0ull);
+    for (size_t n = 0; n < rows; n++) {
+      tab[n * cols] = 1ull;
+      for (size_t j = 1; j < cols && j <= n; j++) tab[n * cols + j] = tab[(n - 1) * cols + j - 1] + tab[(n - 1) * cols + j];
+    }
+    if ((e = cudaMalloc(&ctx->d_binom, tab.size() * sizeof(unsigned long long))) != cudaSuccess)
+      return fail(e, "cudaMalloc");
+    if ((e = cudaMemcpy(ctx->d_binom, tab.data(), tab.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return fail(e, "cudaMemcpy");
+  }
   *out = ctx;
   return KC_OK;
 }
@@ -160,6 +174,7 @@ int kc_destroy(kc_ctx* ctx) {
   ctx->scratch.clear();
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_acc) cudaFree(ctx->d_acc);
+  if (ctx->d_binom) cudaFree(ctx->d_binom);
   if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
   for (auto& ev : ctx->ev)
     if (ev) cudaEventDestroy(ev);

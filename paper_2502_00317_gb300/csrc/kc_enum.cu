@@ -332,6 +332,8 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
     args.depth = k + 1;
     args.prune = ea.prune ? 1 : 0;
     args.memo = ea.memo ? 1 : 0;
+    args.plex = (ea.mode != 1 && !ctx->opts.no_plex) ? 1 : 0;  // counting only
+    args.binom = ctx->d_binom;
     args.out = ea.d_buf;
     args.cap = ea.cap;
     args.acc = ctx->d_acc;
@@ -362,6 +364,7 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
   stt.warp_ns_build = ctx->h_acc[kAccBuildNs];
   stt.warp_ns_busy = ctx->h_acc[kAccBusyNs];
   stt.memo_peak = ctx->h_acc[kAccMemoPeak];
+  stt.plex_frames = ctx->h_acc[kAccPlex];
   if (k >= 2) {
     for (int t = 0; t < kTiers; t++) {
       stt.roots_tier[t] = tier_roots[t];
@@ -510,6 +513,8 @@ int run_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, bool memo, bool pr
     args.depth = kmax + 1;  // stacks deep enough for every query
     args.prune = prune ? 1 : 0;
     args.memo = memo ? 1 : 0;
+    args.plex = (!list && !ctx->opts.no_plex) ? 1 : 0;  // counting only
+    args.binom = ctx->d_binom;
     args.acc = ctx->d_acc;
     args.status = ctx->d_status;
     args.bq = d_q;
@@ -548,6 +553,7 @@ int run_batch(kc_ctx* ctx, const BatchQuery* hq, uint32_t nq, bool memo, bool pr
   stt.warp_ns_build = ctx->h_acc[kAccBuildNs];
   stt.warp_ns_busy = ctx->h_acc[kAccBusyNs];
   stt.memo_peak = ctx->h_acc[kAccMemoPeak];
+  stt.plex_frames = ctx->h_acc[kAccPlex];
   for (int t = 0; t < kTiers; t++) {
     stt.roots_tier[t] = hcnt[t];
     if (hcnt[t]) cudaEventElapsedTime(&stt.ms_tier[t], ctx->ev_tier0[t], ctx->ev_tier1[t]);

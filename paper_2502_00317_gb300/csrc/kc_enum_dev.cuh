@@ -47,6 +47,8 @@ struct EnumKArgs {
   uint32_t k;
   int prune;
   int memo;
+  int plex;                   // count 2-plex candidate sets by their closed form (Sec. VII-A)
+  const unsigned long long* binom;  // C(n, j) mod 2^64, rows of KC_MAX_K + 1 (with plex)
   uint32_t* out;
   unsigned long long cap;
   unsigned long long* acc;
@@ -416,6 +418,7 @@ __device__ __forceinline__ uint32_t lane_count(const uint32_t* R, uint32_t c0, u
 struct Acc {
   unsigned long long cnt = 0, sum = 0;
   uint32_t ops = 0;          // candidate words intersected since the last fold into ops64
+  uint32_t plex = 0;         // frames counted by the 2-plex closed form
   unsigned long long ops64 = 0;
   unsigned long long hits = 0, ins = 0, full = 0, frames = 0;
 };
@@ -434,6 +437,113 @@ enum WarpStat : int {
   kWsCount
 };
 
+// Chunks of 16 bytes each lane keeps in flight while gathering rows (fewer
+// at widths 1 and 2, whose kernels keep to 64 registers).
+__host__ __device__ constexpr int build_unroll(int W) { return W <= 2 ? 2 : 4; }
+
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
+  const uint32_t lo = __shfl_sync(0xFFFFFFFFu, (uint32_t)v, src);
+  const uint32_t hi = __shfl_sync(0xFFFFFFFFu, (uint32_t)(v >> 32), src);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// Step 1 for root u: the rows of G_u.  Row i holds bit j (j > i) when nbr[j]
+// is in N+(nbr[i]).  The warp takes the rows 32 at a time: lane t reads the
+// extent [b, e) of row g + t's out-list, the 16-byte chunks covering all 32
+// lists are numbered consecutively (a warp scan of the chunk counts), and
+// every lane then loads build_unroll(W) chunks at once, finding each chunk's row
+// by a binary search over the lanes' chunk offsets.  A chunk is the aligned
+// 16-byte block holding the entries, so it never leaves the block of a valid
+// entry; entries outside [b, e) are masked.  Each entry w <= nbr[d - 1] is
+// looked up in nbr (ascending: by shuffles at width 1, in shared memory
+// beyond) and sets its bit.  Returns this lane's count of DAG words read.
+template <int W>
+__device__ __forceinline__ uint32_t build_rows(WarpState<W>& st, const EnumKArgs& a, int d) {
+  const uint32_t lane = lane_id();
+  const uint32_t last = st.nbr[d - 1];
+  const uintptr_t addr = (uintptr_t)a.ocol;
+  const uint4* base4 = (const uint4*)(addr & ~(uintptr_t)15);
+  const uint32_t dl = (uint32_t)((addr & 15u) >> 2);  // entry p is word p + dl of base4
+  const uint32_t nb = (W == 1 && (int)lane < d) ? st.nbr[lane] : 0xFFFFFFFFu;
+  int span = 1;  // largest power of two <= d (shared-memory search)
+  while (2 * span <= d) span *= 2;
+  constexpr int kBuildUnroll = build_unroll(W);
+  uint32_t words = 0;
+  for (int g = 0; g < d - 1; g += 32) {
+    const int i = g + (int)lane;
+    uint64_t c0 = 0;    // first chunk of row i's out-list
+    uint32_t meta = 0;  // its first entry's word in that chunk (bits 0..1) and its length (bits 2..)
+    uint32_t nch = 0;   // its chunks
+    if (i < d - 1) {
+      const uint32_t v = st.nbr[i];
+      const uint64_t b = a.orow[v], e = a.orow[v + 1];
+      const uint32_t len = (uint32_t)(e - b);
+      c0 = (b + dl) >> 2;
+      const uint32_t boff = (uint32_t)((b + dl) & 3u);
+      meta = boff | (len << 2);
+      nch = len ? (boff + len + 3) >> 2 : 0u;  // an empty list reads nothing
+      words += len;
+    }
+    uint32_t pre = nch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, pre, o);
+      if ((int)lane >= o) pre += t;
+    }
+    const uint32_t excl = pre - nch;
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, pre, 31);
+    for (uint32_t f0 = 0; f0 < total; f0 += 32 * kBuildUnroll) {
+      uint4 val[kBuildUnroll];
+      uint32_t tag[kBuildUnroll];  // row (bits 0..15) and valid entries (bits 16..19)
+#pragma unroll
+      for (int q = 0; q < kBuildUnroll; q++) {
+        const uint32_t f = f0 + (uint32_t)(q * 32) + lane;
+        int r = 0;  // the largest lane whose first chunk number is <= f
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1)
+          if (__shfl_sync(0xFFFFFFFFu, excl, r + s) <= f) r += s;
+        const uint32_t ci = f - __shfl_sync(0xFFFFFFFFu, excl, r);  // chunk of the row
+        const uint64_t cr = shfl_u64(c0, r);
+        const uint32_t mr = __shfl_sync(0xFFFFFFFFu, meta, r);
+        tag[q] = 0;
+        val[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (f < total) {
+          val[q] = __ldg(base4 + cr + ci);
+          // words 4 ci + x of the row's chunks hold entries when boff <= 4 ci + x < boff + len
+          const uint32_t boff = mr & 3u, len = mr >> 2;
+          uint32_t vm = 0;
+#pragma unroll
+          for (int x = 0; x < 4; x++) vm |= (4 * ci + x >= boff && 4 * ci + x < boff + len) ? (1u << x) : 0u;
+          tag[q] = (uint32_t)(g + r) | (vm << 16);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kBuildUnroll; q++) {
+        const int row = (int)(tag[q] & 0xFFFFu);
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+          const uint32_t w = x == 0 ? val[q].x : (x == 1 ? val[q].y : (x == 2 ? val[q].z : val[q].w));
+          const bool live = ((tag[q] >> (16 + x)) & 1u) && w <= last;
+          if (W == 1) {
+            int j = 0;  // entries of nbr below w (lanes hold nbr, padded with the largest value)
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1)
+              if (__shfl_sync(0xFFFFFFFFu, nb, j + s - 1) < w) j += s;
+            const bool hit = __shfl_sync(0xFFFFFFFFu, nb, j) == w;
+            if (live && hit) atomicOr(&st.rows[row], 1u << j);
+          } else if (live) {
+            int j = 0;
+            for (int s = span; s >= 1; s >>= 1)
+              if (j + s <= d && st.nbr[j + s - 1] < w) j += s;
+            if (j < d && st.nbr[j] == w) atomicOr(&st.rows[(size_t)row * W + (j >> 5)], 1u << (j & 31));
+          }
+        }
+      }
+    }
+  }
+  return words;
+}
+
 // Steps 1 and 2 for root u: bitmap rows, Algorithm 5, masks.  Returns false
 // when the soft-embedding test drops the root.
 template <int W>
@@ -444,52 +554,8 @@ __device__ bool build_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, int
   for (int i = lane; i < d; i += 32) st.nbr[i] = a.ocol[ob + i];
   for (int i = lane; i < d * W; i += 32) st.rows[i] = 0u;
   __syncwarp();
-  const uint32_t last = st.nbr[d - 1];
-  uint32_t words = 0;
-  if (W == 1) {
-    // at most 31 rows: the warp reads each out-list 32 entries at a time and
-    // places each entry by a binary search in nbr (ranks above the row)
-    for (int i = 0; i < d - 1; i++) {
-      const uint32_t v = st.nbr[i];
-      const uint64_t b = a.orow[v], e = a.orow[v + 1];
-      for (uint64_t p0 = b; p0 < e; p0 += 32) {
-        const uint64_t p = p0 + lane;
-        const uint32_t w = p < e ? __ldg(&a.ocol[p]) : 0xFFFFFFFFu;
-        words += (p < e);
-        if (w <= last) {
-          int lo = i + 1, hi = d;
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (st.nbr[mid] < w) lo = mid + 1;
-            else hi = mid;
-          }
-          if (lo < d && st.nbr[lo] == w) atomicOr(&st.rows[(size_t)i * W + (lo >> 5)], 1u << (lo & 31));
-        }
-        if (__all_sync(0xFFFFFFFFu, w > last)) break;
-      }
-    }
-  } else {
-    // one lane per row: row i holds the positions j > i with nbr[j] in
-    // N+(nbr[i]), found by merging the two ascending lists; 32 rows at once
-    for (int i = lane; i < d - 1; i += 32) {
-      const uint32_t v = st.nbr[i];
-      const uint64_t b = a.orow[v], e = a.orow[v + 1];
-      uint32_t* row = st.rows + (size_t)i * W;
-      int j = i + 1;
-      uint64_t p = b;
-      while (p < e && j < d) {
-        const uint32_t w = __ldg(&a.ocol[p]);
-        if (w > last) break;
-        while (j < d && st.nbr[j] < w) j++;
-        if (j < d && st.nbr[j] == w) {
-          row[j >> 5] |= 1u << (j & 31);
-          j++;
-        }
-        p++;
-      }
-      words += (uint32_t)(p - b);
-    }
-  }
+  uint32_t words = build_rows<W>(st, a, d);
+  __syncwarp();
   words = warp_sum(words);
   if (lane == 0) st.stats[kWsWords] += words;
   __syncwarp();
@@ -651,12 +717,88 @@ __device__ bool memo_open(const Memo& memo, const uint32_t (&c)[W], uint32_t cl,
   return false;
 }
 
-// Eq. (1) for a candidate set c needing cl-cliques: 2 cl |E| > (cl - 1) |V|^2.
+// Eq. (1) for a candidate set of sz vertices and e edges needing cl-cliques:
+// 2 cl |E| > (cl - 1) |V|^2.
+__device__ __forceinline__ bool eq1_holds(uint32_t cl, uint32_t sz, uint32_t e) {
+  return 2ull * cl * e > (unsigned long long)(cl - 1) * sz * sz;
+}
+
 template <int W>
 __device__ __forceinline__ bool eq1_dense(const WarpState<W>& st, const uint32_t (&c)[W], uint32_t cl, uint32_t sz,
                                           Acc& acc) {
-  uint32_t e = warp_sum(edges_partial<W>(c, st.rows, acc.ops));
-  return 2ull * cl * e > (unsigned long long)(cl - 1) * sz * sz;
+  return eq1_holds(cl, sz, warp_sum(edges_partial<W>(c, st.rows, acc.ops)));
+}
+
+// The 2-plex early termination DIST applies for large k (Sec. VII-A), for
+// counting.  G[S] is a 2-plex when every vertex of S is non-adjacent to at
+// most one other vertex of S: its p = C(|S|, 2) - e non-edges then form a
+// matching, and an l-clique of G[S] takes from each non-adjacent pair none or
+// one of its two vertices, so G[S] has
+//     sum over j of C(p, j) 2^j C(|S| - 2p, l - j)
+// l-cliques (mod 2^64, with the binomials mod 2^64).  e = |E(S)|.  Returns
+// false when G[S] is not a 2-plex.  The test: no vertex v has two missing
+// vertices above it (M_v = S ∩ (v, ∞) minus row v has at most one member), and
+// the vertices that touch a non-edge -- those with a non-empty M_v and the
+// members of every M_v -- are 2p distinct vertices.  `scratch` holds W words
+// (the sources' bitmap).  Called by the whole warp.
+template <int W>
+__device__ __forceinline__ bool plex2_tail(const WarpState<W>& st, const uint32_t (&S)[W], uint32_t sz, uint32_t l,
+                                       uint32_t p, const unsigned long long* binom, uint32_t* scratch,
+                                       unsigned long long* out) {
+  if (p > 0) {
+    const uint32_t lane = lane_id();
+    bool bad = false;
+    for (int w = 0; w < W; w++) {  // sources: lane's vertex (w, lane)
+      uint32_t cnt = 0;
+      if ((S[w] >> lane) & 1u) {
+        const uint32_t* rv = st.rows + (size_t)((w << 5) + lane) * W;
+        for (int w2 = w; w2 < W; w2++) {
+          const uint32_t above = w2 > w ? 0xFFFFFFFFu : (lane == 31 ? 0u : (0xFFFFFFFFu << (lane + 1)));
+          cnt += __popc(S[w2] & above & ~rv[w2]);
+        }
+      }
+      bad |= cnt > 1;
+      const uint32_t src = __ballot_sync(0xFFFFFFFFu, cnt == 1);
+      if (lane == 0) scratch[w] = src;
+    }
+    if (__any_sync(0xFFFFFFFFu, bad)) return false;
+    __syncwarp();
+    uint32_t touched = 0;  // |sources ∪ members of the M_v|
+    for (int w2 = 0; w2 < W; w2++) {
+      uint32_t m = 0;
+      for (int w = 0; w <= w2; w++) {
+        if ((S[w] >> lane) & 1u) {
+          const uint32_t above = w2 > w ? 0xFFFFFFFFu : (lane == 31 ? 0u : (0xFFFFFFFFu << (lane + 1)));
+          m |= S[w2] & above & ~st.rows[(size_t)((w << 5) + lane) * W + w2];
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xFFFFFFFFu, m, o);
+      touched += __popc(m | scratch[w2]);
+    }
+    __syncwarp();
+    if (touched != 2 * p) return false;
+  }
+  constexpr int kCols = KC_MAX_K + 1;
+  const uint32_t free_v = sz - 2 * p;
+  unsigned long long t = 0;
+  for (uint32_t j = 0; j <= p && j <= l; j++) {
+    if (l - j > free_v) continue;
+    t += binom[(size_t)p * kCols + j] * (1ull << j) * binom[(size_t)free_v * kCols + (l - j)];
+  }
+  *out = t;
+  return true;
+}
+
+// The quick part of the test first: a 2-plex has at most |S| / 2 non-edges.
+template <int W>
+__device__ __forceinline__ bool plex2_count(const WarpState<W>& st, const uint32_t (&S)[W], uint32_t sz, uint32_t l,
+                                            uint32_t e, const unsigned long long* binom, uint32_t* scratch,
+                                            unsigned long long* out) {
+  if (sz < l || sz < 2) return false;
+  const unsigned long long pairs = (unsigned long long)sz * (sz - 1) / 2;
+  if (e > pairs || 2 * (pairs - e) > sz) return false;
+  return plex2_tail<W>(st, S, sz, l, (uint32_t)(pairs - e), binom, scratch, out);
 }
 
 // Plain depth-first search (MODE 0 count, MODE 1 list) below the frame at
@@ -777,6 +919,19 @@ __device__ void dfs_plain(WarpState<W>& st, const EnumKArgs& a, int base, Acc& a
     if (lane == 0) acc.ops += W;
     __syncwarp();
     if (lane == 0) st.pos[depth] = v - 1;
+    if (MODE == 0 && a.plex && l - 1 >= 4 && sz >= l - 1 && anym) {
+      // a child set that is a 2-plex is counted in closed form (Sec. VII-A)
+      const uint32_t e = warp_sum(edges_partial<W>(c, st.rows, acc.ops));
+      unsigned long long pv = 0;
+      if (plex2_count<W>(st, c, sz, l - 1, e, a.binom, st.crow, &pv)) {
+        if (lane == 0) {
+          acc.cnt += pv;
+          acc.plex++;
+        }
+        __syncwarp();
+        continue;
+      }
+    }
     if (sz >= l - 1 && anym) {
       if (lane < W) st.cand[(depth + 1) * W + lane] = word_at<W>(c, lane);
       if (lane == 0) {
@@ -876,15 +1031,21 @@ __device__ unsigned long long dfs_memo(WarpState<W>& st, const EnumKArgs& a, con
 #pragma unroll
       for (int w = 0; w < W; w++) anym |= c[w] & mk[w];
       if (sz >= cl && anym) {
-        cd = fd || (a.memo && eq1_dense<W>(st, c, cl, sz, acc));
-        if (!cd && sz <= 32 && cl <= kCompactMaxL) {
-          val = warp_sum(count_compact<W>(st, c, sz, cl, acc.ops));
-        } else if (cd) {
-          if (memo_open<W>(memo, c, cl, &start_sum, &start_pos, acc)) val = start_sum;
-          else resolved = false;
+        // |E(c)| for the 2-plex test and Eq. (1) (below a dense frame Eq. (1) is not needed)
+        const uint32_t e = (a.plex || (a.memo && !fd)) ? warp_sum(edges_partial<W>(c, st.rows, acc.ops)) : 0u;
+        if (a.plex && plex2_count<W>(st, c, sz, cl, e, a.binom, st.crow, &val)) {
+          if (lane == 0) acc.plex++;
         } else {
-          resolved = false;
-          start_pos = top_bit<W>(c);
+          cd = fd || (a.memo && eq1_holds(cl, sz, e));
+          if (!cd && sz <= 32 && cl <= kCompactMaxL) {
+            val = warp_sum(count_compact<W>(st, c, sz, cl, acc.ops));
+          } else if (cd) {
+            if (memo_open<W>(memo, c, cl, &start_sum, &start_pos, acc)) val = start_sum;
+            else resolved = false;
+          } else {
+            resolved = false;
+            start_pos = top_bit<W>(c);
+          }
         }
       }
     }
@@ -1226,6 +1387,7 @@ __device__ __forceinline__ void acc_add(Acc& to, const Acc& from) {
   to.ins += from.ins;
   to.full += from.full;
   to.frames += from.frames;
+  to.plex += from.plex;
 }
 
 // The definitions, for the width's own translation unit.  A search reached
@@ -1435,9 +1597,25 @@ __device__ __forceinline__ void run_branch_body(WarpState<W>& st, const EnumKArg
     for (int w = 0; w < W; w++) anym |= c[w] & mk[w];
     if (!anym) return;
   }
+  // a branch whose set is a 2-plex is counted in closed form (Sec. VII-A)
+  uint32_t e = 0;
+  bool have_e = false;
+  if (!is_list(MODE) && a.plex && cl >= 4) {
+    e = warp_sum(edges_partial<W>(c, st.rows, acc.ops));
+    have_e = true;
+    unsigned long long pv = 0;
+    if (plex2_count<W>(st, c, sz, cl, e, a.binom, st.crow, &pv)) {
+      if (lane == 0) {
+        acc.cnt += pv;
+        acc.plex++;
+      }
+      return;
+    }
+  }
   // Eq. (1) for the branch's frame; below a dense frame every frame is
   // memoised (Algorithm 3 recurses into itself)
-  const bool cd = uses_trie(MODE) && cl > 3 && (parent_dense || (a.memo && eq1_dense<W>(st, c, cl, sz, acc)));
+  const bool cd = uses_trie(MODE) && cl > 3 &&
+                  (parent_dense || (a.memo && (have_e ? eq1_holds(cl, sz, e) : eq1_dense<W>(st, c, cl, sz, acc))));
   if (!is_list(MODE) && cl >= 3 && cl <= kCompactMaxL && sz <= 32 && !cd) {
     acc.cnt += count_compact<W>(st, c, sz, cl, acc.ops);
     return;
@@ -1606,6 +1784,7 @@ __device__ void flush_acc(const EnumKArgs& a, Acc& acc, const unsigned long long
   unsigned long long cnt = warp_sum(acc.cnt);
   unsigned long long sum = warp_sum(acc.sum);
   unsigned long long ops = warp_sum(acc.ops64 + acc.ops);
+  const unsigned long long plex = warp_sum((unsigned long long)acc.plex);
   if (lane == 0) {
     if (ops) atomicAdd(&a.acc[kAccWordOps], ops);
     if (cnt) atomicAdd(&a.acc[kAccCount], cnt);
@@ -1616,6 +1795,7 @@ __device__ void flush_acc(const EnumKArgs& a, Acc& acc, const unsigned long long
     if (acc.ins) atomicAdd(&a.acc[kAccMemoInserts], acc.ins);
     if (acc.full) atomicAdd(&a.acc[kAccMemoFull], acc.full);
     if (acc.frames) atomicAdd(&a.acc[kAccMemoFrames], acc.frames);
+    if (plex) atomicAdd(&a.acc[kAccPlex], plex);
     if (ws[kWsHeavy]) atomicAdd(&a.acc[kAccRootsHeavy], ws[kWsHeavy]);
     if (ws[kWsTasks]) atomicAdd(&a.acc[kAccTasks], ws[kWsTasks]);
     if (ws[kWsBuildNs]) atomicAdd(&a.acc[kAccBuildNs], ws[kWsBuildNs]);
@@ -1691,13 +1871,24 @@ __device__ void root_body(WarpState<W>& st, const EnumKArgs& a, Memo& memo, uint
       __syncwarp();
     }
   }
-  // Eq. (1) on G_u for the root frame
+  // Eq. (1) on G_u for the root frame; a root whose G_u is a 2-plex is
+  // counted in closed form (Sec. VII-A)
   bool dense0 = false;
-  if (uses_trie(MODE) && a.memo && need > 3) {
+  if ((uses_trie(MODE) && a.memo && need > 3) || (!is_list(MODE) && a.plex && need >= 4)) {
     uint32_t er = 0;
     for (int i = lane; i < d * W; i += 32) er += __popc(st.rows[i]);
     er = warp_sum(er);
-    dense0 = 2ull * need * er > (unsigned long long)(need - 1) * d * d;
+    if (!is_list(MODE) && a.plex && need >= 4) {
+      unsigned long long pv = 0;
+      if (plex2_count<W>(st, S0, (uint32_t)d, need, er, a.binom, st.crow, &pv)) {
+        if (lane == 0) {
+          acc.cnt += pv;
+          acc.plex++;
+        }
+        return;
+      }
+    }
+    dense0 = uses_trie(MODE) && a.memo && need > 3 && eq1_holds(need, (uint32_t)d, er);
   }
   // EdgeParallel (Sec. VII-D) as the whole decomposition: every root's
   // first-level branches (u, v1) are tasks of the second phase

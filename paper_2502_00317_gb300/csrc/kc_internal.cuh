@@ -144,6 +144,7 @@ struct kc_ctx {
   uint32_t* d_status = nullptr;           // device status bits
   unsigned long long* d_acc = nullptr;    // device accumulators (count, checksum, written, stats ...)
   unsigned long long* h_acc = nullptr;    // pinned host mirror
+  unsigned long long* d_binom = nullptr;  // C(n, j) mod 2^64 for n <= KC_MAX_OUTDEG, j <= KC_MAX_K (2-plex counts)
   cudaEvent_t ev[16] = {};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[kc::kTiers] = {};
@@ -180,6 +181,7 @@ enum AccSlot : int {
   kAccBuildNs,     // warp-nanoseconds spent building root bit-matrices (a5)
   kAccBusyNs,      // warp-nanoseconds spent on roots and tasks in all
   kAccMemoPeak,    // most trie entries stored for one root
+  kAccPlex,        // frames counted by the 2-plex closed form
   kAccQueue0,      // root-queue counters (one per width tier)
   kAccArena0 = kAccQueue0 + kTiers,     // split path: arena units used, per tier
   kAccTaskUsed0 = kAccArena0 + kTiers,  // split path: tasks queued, per tier

@@ -177,6 +177,48 @@ def disjoint_cliques(sizes) -> Graph:
     return g
 
 
+def complete_minus(n: int, missing) -> Graph:
+    """K_n without the listed vertex pairs (a matching of them makes a 2-plex)."""
+    gone = {(min(a, b), max(a, b)) for a, b in missing}
+    i, j = np.triu_indices(n, 1)
+    keep = np.array([(int(x), int(y)) not in gone for x, y in zip(i, j)], dtype=bool)
+    g = csr_from_pairs(n, i[keep], j[keep])
+    g.name = f"K{n}-{sorted(gone)}"
+    return g
+
+
+def planted_plexes(n: int = 6000, p: float = 0.002, n_sets: int = 24, smin: int = 12, smax: int = 26,
+                   seed: int = 9) -> Graph:
+    """Sparse G(n, p) background plus planted near-cliques on random vertex
+    sets: each is complete minus some vertex pairs.  Set i removes a random
+    matching of up to s/2 pairs (a 2-plex) when i % 3 != 2, and otherwise a
+    matching plus one extra pair that shares a vertex with it (not a 2-plex).
+    Ids are randomly permuted."""
+    bg = er_gnp(n, p, seed)
+    a0, b0 = edges_of(bg)
+    cg = _stream(seed, 11)
+    pa, pb = [a0], [b0]
+    for idx in range(n_sets):
+        s = smin + int(_bounded(_raw(cg, 1), smax - smin + 1)[0])
+        order = np.argsort(_raw(cg, n), kind="stable")[:s]
+        mem = order.astype(np.int64)
+        pairs = int(_bounded(_raw(cg, 1), s // 2 + 1)[0])
+        gone = {(int(mem[2 * t]), int(mem[2 * t + 1])) for t in range(pairs)}
+        if idx % 3 == 2 and s >= 3:
+            gone.add((int(mem[0]), int(mem[2])))
+        i, j = np.triu_indices(s, 1)
+        keep = np.array([(int(mem[x]), int(mem[y])) not in gone and (int(mem[y]), int(mem[x])) not in gone
+                         for x, y in zip(i, j)], dtype=bool)
+        pa.append(mem[i][keep])
+        pb.append(mem[j][keep])
+    perm = _random_permutation(seed, 12, n)
+    a = perm[np.concatenate(pa)]
+    b = perm[np.concatenate(pb)]
+    g = csr_from_pairs(n, a, b)
+    g.name = f"plexes(n={n},sets={n_sets},seed={seed})"
+    return g
+
+
 def er_gnp(n: int, p: float, seed: int) -> Graph:
     """Erdos-Renyi G(n, p): each pair i < j drawn independently.
 

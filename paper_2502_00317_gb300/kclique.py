@@ -68,6 +68,7 @@ class kc_opts(ctypes.Structure):
         ("decomposition", ctypes.c_uint32),
         ("autotune", ctypes.c_uint32),
         ("tune_cache", ctypes.c_char_p),
+        ("no_plex", ctypes.c_uint32),
     ]
 
 
@@ -116,6 +117,7 @@ class kc_stats(ctypes.Structure):
         ("warp_ns_build", ctypes.c_uint64),
         ("warp_ns_busy", ctypes.c_uint64),
         ("memo_peak", ctypes.c_uint64),
+        ("plex_frames", ctypes.c_uint64),
     ]
 
 
@@ -250,9 +252,10 @@ def kc_strerror(status: int) -> str:
 
 def kc_create(device: int = 0, no_memo: bool = False, no_prune: bool = False, memo_bytes: int = 0,
               spin_limit: int = 0, split_threshold: int = 0, decomposition: int = 0, autotune: bool = False,
-              tune_cache: str | None = None) -> int:
+              tune_cache: str | None = None, no_plex: bool = False) -> int:
     o = kc_opts(ctypes.sizeof(kc_opts), int(no_memo), int(no_prune), int(split_threshold), int(memo_bytes),
-                int(spin_limit), int(decomposition), int(autotune), tune_cache.encode() if tune_cache else None)
+                int(spin_limit), int(decomposition), int(autotune), tune_cache.encode() if tune_cache else None,
+                int(no_plex))
     h = ctypes.c_void_p()
     _check(load().kc_create(ctypes.byref(h), int(device), ctypes.byref(o)), "kc_create")
     return h.value

@@ -239,6 +239,41 @@ def test_listing_trie_replays_and_matches_oracle(ctx, ctx_plain, maker, ks, dens
             c.free(h)
 
 
+@pytest.mark.parametrize("maker,ks,plex", [
+    (lambda: gg.planted_plexes(), range(3, 11), True),
+    (lambda: gg.complete_minus(30, [(0, 1), (2, 3), (4, 5), (6, 7)]), range(3, 11), True),  # a 2-plex at the root
+    (lambda: gg.complete_minus(30, [(0, 1), (1, 2)]), range(3, 11), False),  # vertex 1 misses two
+    (lambda: gg.turan(24, 12), range(3, 11), True),  # K_24 minus a perfect matching
+    (lambda: gg.complete_minus(70, [(3, 40), (41, 69)]), range(3, 6), True),  # three words
+])
+def test_two_plex_closed_form_matches_oracle(maker, ks, plex):
+    """The 2-plex early termination (Sec. VII-A): a candidate set whose
+    non-edges form a matching is counted by its closed form.  Counts equal
+    the oracle's with it on and off, with the memo on and off; with it on,
+    frames are counted that way."""
+    g = maker()
+    og = oracle.OracleGraph.from_graph(g)
+    ctxs = [kc.Context(0), kc.Context(0, no_plex=True), kc.Context(0, no_memo=True),
+            kc.Context(0, no_memo=True, no_prune=True, no_plex=True)]
+    hs = [c.upload_host(g.n, g.rowptr, g.col) for c in ctxs]
+    try:
+        used = 0
+        for k in ks:
+            want = og.count(k)[0]
+            for i, (c, h) in enumerate(zip(ctxs, hs)):
+                assert c.count(h, k) == want, (g.name, k, i)
+                st = c.stats()
+                if i in (1, 3):
+                    assert st["plex_frames"] == 0
+                elif i == 0:
+                    used += st["plex_frames"]
+        assert (used > 0) or not plex, g.name
+    finally:
+        for c, h in zip(ctxs, hs):
+            c.free(h)
+            c.close()
+
+
 @pytest.mark.parametrize("maker,splits", [
     (lambda: gg.chung_lu_planted(n=20000, n_cliques=40, seed=1), False),  # wide roots are dense: memo, no split
     (lambda: gg.rgg_torus(4000, 70.0, seed=6), True),
@@ -285,19 +320,22 @@ def test_edge_parallel_decomposition_matches_oracle(maker):
     """EdgeParallel as the whole decomposition (Sec. VII-D): every root's
     first-level branches (u, v) are separate tasks of the second launch, in
     every width tier; counts with and without the memo, checksums and the
-    listed tuples equal the oracle's."""
+    listed tuples equal the oracle's.  (A root whose G_u is a 2-plex is
+    counted whole by its closed form, so the split invariant is checked with
+    that off.)"""
     g = maker()
     og = oracle.OracleGraph.from_graph(g)
-    ctxs = [kc.Context(0, decomposition=kc.KC_EDGE_PARALLEL),
-            kc.Context(0, decomposition=kc.KC_EDGE_PARALLEL, no_memo=True)]
+    ctxs = [kc.Context(0, decomposition=kc.KC_EDGE_PARALLEL, no_plex=True),
+            kc.Context(0, decomposition=kc.KC_EDGE_PARALLEL, no_memo=True, no_plex=True),
+            kc.Context(0, decomposition=kc.KC_EDGE_PARALLEL)]
     try:
         hs = [c.upload_host(g.n, g.rowptr, g.col) for c in ctxs]
         for k in (3, 4, 5, 6, 7):
             want = og.count(k)[0]
-            for c, h in zip(ctxs, hs):
+            for i, (c, h) in enumerate(zip(ctxs, hs)):
                 assert c.count(h, k) == want, (k, c.stats())
                 st = c.stats()
-                if want:  # every root that survives pruning was split into its branches
+                if want and i < 2:  # every root that survives pruning was split into its branches
                     assert st["roots_heavy"] == st["roots_total"] - st["roots_pruned"] > 0, st
         for k in (3, 5):
             assert ctxs[0].list(hs[0], k, None, 0)[1:] == og.checksum(k), k

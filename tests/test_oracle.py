@@ -114,6 +114,19 @@ def test_disjoint_cliques_sum_of_binomials():
         assert og.count(k)[0] == sum(oracle.binom(s, k) for s in sizes)
 
 
+@pytest.mark.parametrize("n,p", [(12, 3), (16, 8), (25, 5), (9, 0)])
+def test_complete_minus_matching_closed_form(n, p):
+    """K_n without a matching of p pairs (a 2-plex): a k-clique takes from
+    each missing pair none or one of its two vertices, and any of the n - 2p
+    others, so there are sum over j of C(p, j) 2^j C(n - 2p, k - j)."""
+    from math import comb
+
+    og = oracle.OracleGraph.from_graph(gg.complete_minus(n, [(2 * t, 2 * t + 1) for t in range(p)]))
+    for k in range(1, n + 1):
+        want = sum(comb(p, j) * 2 ** j * comb(n - 2 * p, k - j) for j in range(min(p, k) + 1))
+        assert og.count(k)[0] == want, (n, p, k)
+
+
 # ------------------------------------------------------------ brute force
 @pytest.mark.parametrize("seed", range(12))
 def test_random_tiny_graphs_brute_force(seed):

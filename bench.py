@@ -34,6 +34,7 @@ UNIT = "k-cliques/s"
 WORKLOAD = "chung_lu_n1e6_g2.1_d20_planted2000x[20,60]_seed1"
 KS = (5, 6, 7, 8, 9)
 L2_BYTES = 129 * 1024 * 1024
+ENUM_TRAFFIC = None
 
 
 def _args():
@@ -255,9 +256,10 @@ def run_ours(a):
         "peak_source": peak_note,
         "unit": "Gword-op/s (word-op = 32-bit AND + POPC of candidate words)",
         "frac": round(achieved * 1e9 / peak_ops, 5) if (achieved and peak_ops) else None,
-        # DRAM bytes of the family per kc_count call, from one ncu capture of this sweep:
-        # dram__bytes_read.sum + dram__bytes_write.sum over k_enum + k_tasks, averaged per call
-        "traffic": 616778223 if (not a.small and ks == KS) else None,
+        # DRAM bytes of the family per kc_count call (dram__bytes_read.sum +
+        # dram__bytes_write.sum over its kernels) from an ncu capture of the
+        # current kernels; null while no such capture exists
+        "traffic": ENUM_TRAFFIC if (not a.small and ks == KS) else None,
         "traffic_unit": "bytes per kc_count call (enumerator family)",
         "word_ops_per_launch": round(word_ops / calls),
         "ms_per_launch": round(enum_ms / calls, 3),
@@ -657,14 +659,30 @@ def run_rmat(a):
     info = ctx.info(h)
     _, _, orow, _ = ctx.export_dag(h)
     d = np.diff(orow.astype(np.int64))
-    lo = int(np.argmax(d >= 512)) if (d >= 512).any() else int(np.argmax(d))
-    w, total = 64, 0
-    while True:
-        hi = min(info["n"], lo + w)
-        _, total, _ = ctx.list_range(h, k, lo, hi, None, 0, stream)
-        if total >= a.chunk or hi == info["n"]:
-            break
-        w *= 2
+    # the chunk: from the first rank of out-degree >= T, widened (doubling,
+    # then halving back) until it holds about --chunk cliques; T falls from
+    # 512 (16-word roots) while one root alone holds more than 4 chunks
+    lo = hi = 0
+    total = 0
+    for thr in (512, 256, 128, 64, 32, 0):
+        if not (d >= thr).any():
+            continue
+        lo = int(np.argmax(d >= thr))
+        _, one, _ = ctx.list_range(h, k, lo, lo + 1, None, 0, stream)
+        if one > 4 * a.chunk and thr > 0:
+            continue
+        w, total = 1, one
+        while total < a.chunk and lo + w < info["n"]:
+            w = min(2 * w, info["n"] - lo)
+            _, total, _ = ctx.list_range(h, k, lo, lo + w, None, 0, stream)
+        step = w // 4
+        while total > 2 * a.chunk and step >= 1:
+            _, t2, _ = ctx.list_range(h, k, lo, lo + w - step, None, 0, stream)
+            if t2 >= a.chunk // 2:
+                w, total = w - step, t2
+            step //= 2
+        hi = lo + w
+        break
     buf = torch.empty(max(total * k, 1), dtype=torch.int32, device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
     for _ in range(a.warmup):
@@ -698,6 +716,7 @@ def run_rmat(a):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32/u64 (exact integer)", "data": "synthetic (seeded generator)",
         "config": {"workload": "rmat_scale22_ef16_abcd.57.19.19.05_seed2_k6", "ranks": [lo, hi],
+                   "out_degree_first_root": int(d[lo]),
                    "chunk_cliques": total, "checksum": ref[2], "buffer_bytes": 4 * k * total,
                    "l2": "flushed between timed steps"},
         "graph": info, "upload_s": upload_s, "upload_stage_ms": up,
@@ -717,8 +736,9 @@ def run_rmat(a):
 
 
 def run_ablation(a):
-    """NEXT-3 (Sec. VII-C's baseline / memo / memo + pruning comparison, and
-    the decomposition of Sec. VII-D): each variant counts config 2 for
+    """NEXT-3 (Sec. VII-C's baseline / memo / memo + pruning comparison, the
+    2-plex early termination of Sec. VII-A, and the decomposition of Sec.
+    VII-D): each variant counts config 2 for
     k = 5..9 (the memo-off variants up to k = 7) and config 3 for k = 5; per
     count its enumeration time, candidate words intersected and the most trie
     entries stored for one root."""
@@ -729,7 +749,8 @@ def run_ablation(a):
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
-    variants = [("default", {}), ("no_prune", {"no_prune": True}), ("no_split", {"split_threshold": 0xFFFFFFFF}),
+    variants = [("default", {}), ("no_plex", {"no_plex": True}), ("no_prune", {"no_prune": True}),
+                ("no_split", {"split_threshold": 0xFFFFFFFF}),
                 ("no_memo", {"no_memo": True}), ("baseline", {"no_memo": True, "no_prune": True}),
                 ("edge_parallel", {"decomposition": kc.KC_EDGE_PARALLEL}),
                 ("edge_parallel_no_memo", {"decomposition": kc.KC_EDGE_PARALLEL, "no_memo": True})]

@@ -567,12 +567,22 @@ def test_bounded_wait_gives_up_and_context_stays_usable():
         c.free(h)
 
 
+_RMAT22 = []
+
+
+def _rmat22():
+    """Config 3's graph, generated once per test session (about a minute)."""
+    if not _RMAT22:
+        _RMAT22.append(gg.config_rmat())
+    return _RMAT22[0]
+
+
 def test_rmat_scale22_full_size_vs_golden(ctx):
     """R-MAT scale 22 (raw pairs, canonicalised on the device): m, degeneracy,
     the k = 3 and 4 counts and checksums and the k = 5 count against the
     oracle's stored values; k = 4 also as a sum over a partition of root ranges."""
     gold = json.load(open(os.path.join(GOLD, "config_results.json")))
-    g = gg.config_rmat()
+    g = _rmat22()
     assert gold["rmat_22_16_seed2_k3"]["fingerprint"] == g.fingerprint()
     h = ctx.upload_host(g.n, g.rowptr, g.col, canonicalize=True)
     try:
@@ -636,3 +646,105 @@ def test_rmat_k6_vs_oracle(opts):
                 c.free(h)
     finally:
         c.close()
+
+
+def _induced(n, rank, orow, ocol, ranks):
+    """The subgraph induced by the vertices of the given ranks, in original ids
+    (on all n ids; the others are isolated)."""
+    vert = np.empty(n, dtype=np.int64)
+    vert[rank.astype(np.int64)] = np.arange(n, dtype=np.int64)
+    orow = orow.astype(np.int64)
+    ranks = np.unique(np.asarray(ranks, dtype=np.int64))
+    lens = orow[ranks + 1] - orow[ranks]
+    rows = np.repeat(ranks, lens)
+    first = np.repeat(orow[ranks] - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens)
+    cols = ocol[first + np.arange(rows.size)].astype(np.int64)
+    sel = np.isin(cols, ranks)
+    return gg.csr_from_pairs(n, vert[rows[sel]], vert[cols[sel]])
+
+
+def test_rmat_scale22_k6_dense_core():
+    """Config 3 at full size, k = 6 (listing with checksum).  Listing all of its
+    3.3e14 6-cliques costs as many hash chains, so the full-size checks take
+    parts of the graph whose listing is checkable by other routes:
+
+    - the top X ranks of the DAG's order (the innermost core): out-neighbours
+      have higher ranks, so kc_list_range(n - X, n) lists exactly the 6-cliques
+      of the subgraph the top X ranks induce;
+    - one wide root u (out-degree > 256, a 16- or 32-word root, searched in
+      narrow re-indexed branches): its cliques are those of G[{u} + N+(u)]
+      minus those of G[N+(u)].
+
+    Each subgraph is counted and listed (total + checksum) in separate contexts
+    with the memo, pruning, heavy-root split, 2-plex closed form and the
+    decomposition toggled, and by the oracle; the top range also splits into
+    sub-ranges whose totals add and checksums wrap-add."""
+    g = _rmat22()
+    k = 6
+    c = kc.Context(0)
+    try:
+        h = c.upload_host(g.n, g.rowptr, g.col, canonicalize=True)
+        n = c.info(h)["n"]
+        _, rank, orow, ocol = c.export_dag(h)
+        d = np.diff(orow.astype(np.int64))
+
+        def top(x):
+            return c.list_range(h, k, n - x, n)
+
+        x = 16
+        while x * 2 <= n and top(x * 2)[1] <= (1 << 24):
+            x *= 2
+        _, t_top, s_top = top(x)
+        assert t_top > 0
+        cuts = [n - x, n - x // 2, n - x // 8, n]
+        tot, chk = 0, 0
+        for lo, hi in zip(cuts, cuts[1:]):
+            _, t, s = c.list_range(h, k, lo, hi)
+            tot += t
+            chk = (chk + s) % (1 << 64)
+        assert (tot, chk) == (t_top, s_top)
+        # the wide root: of the 64 narrowest roots of out-degree > 256, the
+        # first with at most 2^27 cliques of its own and at most 2^28 in its
+        # out-neighbourhood
+        u = None
+        wide = np.flatnonzero(d > 256)
+        for cand in wide[np.argsort(d[wide], kind="stable")][:64]:
+            _, t_u, s_u = c.list_range(h, k, int(cand), int(cand) + 1)
+            if not 0 < t_u <= (1 << 27):
+                continue
+            nbrs = ocol[int(orow[cand]):int(orow[cand + 1])].astype(np.int64)
+            base = _induced(n, rank, orow, ocol, nbrs)
+            hb = c.upload_host(base.n, base.rowptr, base.col)
+            t_b = c.count(hb, k)
+            c.free(hb)
+            if t_b <= (1 << 28):
+                u = int(cand)
+                break
+        assert u is not None, "no 16- or 32-word root with a small clique count"
+        c.free(h)
+    finally:
+        c.close()
+    print(f"config 3, k = 6: top {x} ranks hold {t_top} cliques (checksum {s_top:#x}); root of rank {u} "
+          f"(out-degree {d[u]}) holds {t_u} (checksum {s_u:#x}), its out-neighbourhood {t_b}")
+    top_g = _induced(n, rank, orow, ocol, np.arange(n - x, n))
+    apex = _induced(n, rank, orow, ocol, np.concatenate([[u], nbrs]))
+    assert oracle.OracleGraph.from_graph(top_g).checksum(k) == (t_top, s_top)
+    oa = oracle.OracleGraph.from_graph(apex).checksum(k)
+    ob = oracle.OracleGraph.from_graph(base).checksum(k)
+    assert (oa[0] - ob[0], (oa[1] - ob[1]) % (1 << 64)) == (t_u, s_u)
+    for opts in ({}, {"no_memo": True}, {"no_prune": True}, {"split_threshold": 1}, {"no_plex": True},
+                 {"decomposition": kc.KC_EDGE_PARALLEL}):
+        cv = kc.Context(0, **opts)
+        try:
+            got = []
+            for sub in (top_g, apex, base):
+                hv = cv.upload_host(sub.n, sub.rowptr, sub.col)
+                cnt = cv.count(hv, k)
+                _, t, s = cv.list(hv, k, None, 0)
+                assert cnt == t, opts
+                got.append((t, s))
+                cv.free(hv)
+            assert got[0] == (t_top, s_top), opts
+            assert got[1] == oa and got[2] == ob, opts
+        finally:
+            cv.close()

@@ -749,7 +749,8 @@ def run_ablation(a):
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
-    variants = [("default", {}), ("no_plex", {"no_plex": True}), ("no_prune", {"no_prune": True}),
+    variants = [("default", {}), ("memo_every_k", {"memo_min_k": 3}), ("no_plex", {"no_plex": True}),
+                ("no_prune", {"no_prune": True}),
                 ("no_split", {"split_threshold": 0xFFFFFFFF}),
                 ("no_memo", {"no_memo": True}), ("baseline", {"no_memo": True, "no_prune": True}),
                 ("edge_parallel", {"decomposition": kc.KC_EDGE_PARALLEL}),

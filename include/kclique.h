@@ -56,7 +56,8 @@ typedef struct kc_opts {
   uint32_t no_prune;       /* 1: never prune by soft embeddings (Sec. V, Algorithm 5) */
   uint32_t split_threshold;/* a root of width > 32 whose G_u has more wedges (sum of C(out-degree, 2)) than
                               this is split into one task per first-level branch (Sec. VII-D);
-                              0: default 16384, 0xFFFFFFFF: never split; applies for k >= 5 */
+                              0: default 16384 for k >= 6; 0xFFFFFFFF: never split; a value set here
+                              (or by the autotuner) applies for k >= 5 */
   uint64_t memo_bytes;     /* device bytes for the memo tables (0: default 1 GiB); the tau of Sec. VI */
   uint64_t spin_limit;     /* nanoseconds before a device-side wait gives up with KC_E_DEVICE_TIMEOUT
                               (0: default 2 s) */
@@ -69,6 +70,10 @@ typedef struct kc_opts {
                               variable KC_TUNE_CACHE, else memory only); read at kc_create, appended to */
   uint32_t no_plex;        /* 1: never count a 2-plex subgraph by its closed form (the 2-plex early
                               termination of Sec. VII-A); counting only, listing never uses it */
+  uint32_t memo_min_k;     /* kc_count uses the memo (unless no_memo) for k >= this; 0: the default, 8 with
+                              the 2-plex closed form on and 3 with it off (with the closed form taking the
+                              dense cliques, the memo's bookkeeping costs more than it saves below k = 8);
+                              listing and kc_count_batched are not affected */
 } kc_opts;
 
 #define KC_NODE_PARALLEL 0u

@@ -340,7 +340,13 @@ int run_enum(kc_ctx* ctx, const DevGraph& g, const EnumArgs& ea, cudaStream_t s)
     args.status = ctx->d_status;
     uint32_t* troots[kTiers];
     for (int t = 0; t < kTiers; t++) troots[t] = lists + (size_t)t * lcap;
-    KC_TRY(launch_tiers(ctx, args, hcnt, troots, nullptr, mode, k >= 5, s, &launches, &enum_launches));
+    // the default split starts at k = 6: at k = 5 a heavy root's branches
+    // hold too little below them to pay for publishing it (config 2: 6.6 ms
+    // unsplit against 8.7 ms split); a threshold the caller or the autotuner
+    // sets applies from k = 5
+    const bool split_set = ctx->tuning.split != 0 || ctx->opts.split_threshold != 0;
+    KC_TRY(launch_tiers(ctx, args, hcnt, troots, nullptr, mode, k >= (split_set ? 5u : 6u), s, &launches,
+                        &enum_launches));
     for (int t = 0; t < kTiers; t++) tier_roots[t] = hcnt[t];
     KC_CUDA(cudaEventRecord(ev[7], s));
   }

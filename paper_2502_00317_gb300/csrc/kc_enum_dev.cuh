@@ -544,6 +544,76 @@ __device__ __forceinline__ uint32_t build_rows(WarpState<W>& st, const EnumKArgs
   return words;
 }
 
+// Largest j < p whose bit is set in B (and in A, when A is not null), or -1.
+template <int W>
+__device__ __forceinline__ int top_below(const uint32_t* A, const uint32_t* B, int p) {
+  if (p <= 0) return -1;
+  uint32_t lim = (p & 31) ? ((1u << (p & 31)) - 1u) : 0xFFFFFFFFu;
+  for (int w = (p - 1) >> 5; w >= 0; w--) {
+    uint32_t x = B[w] & lim;
+    if (A) x &= A[w];
+    if (x) return (w << 5) + 31 - __clz(x);
+    lim = 0xFFFFFFFFu;
+  }
+  return -1;
+}
+
+// Algorithm 5 (soft embeddings, Sec. V) over the root's d local vertices,
+// r capped at rcap; writes st.rr[0..d) and returns r of the root itself.
+// Algorithm 5 walks a vertex's out-neighbours from the largest down with a
+// counter c = 1 and increments c at each neighbour whose r is at least c.
+// The neighbour where c reaches t + 1 is therefore the largest neighbour
+// below the one where c reached t whose r is at least t.  Writing B_t for the
+// vertices with r >= t, B_{t+1} follows from B_t alone: a vertex is in B_{t+1}
+// when its row, restricted to B_t and below its previous increment point p,
+// is not empty, and its new p is that set's top bit.  So all rows advance
+// together, one round per t (lane = row), instead of one vertex after
+// another; the root's own walk is the same over all d vertices.  B_t is kept
+// in st.masks[t] (the masks of the search, which it equals for t < k) and
+// each row's p in st.pidx (unused by a root's own state).  Same values as
+// the vertex-by-vertex form: rows only hold larger vertices, and each B_t is
+// complete before round t reads it.
+template <int W>
+__device__ uint32_t soft_embedding(WarpState<W>& st, int d, uint32_t rcap) {
+  const uint32_t lane = lane_id();
+  if (lane < W) {
+    const int lo = (int)lane << 5;
+    st.masks[W + lane] = d >= lo + 32 ? 0xFFFFFFFFu : (d > lo ? ((1u << (d - lo)) - 1u) : 0u);
+  }
+  for (int i = (int)lane; i < d; i += 32) {
+    st.pidx[i] = (uint16_t)d;  // no increment point yet: the whole row
+    st.rr[i] = 1;
+  }
+  __syncwarp();
+  int q = d;  // the root's walk (the same on every lane)
+  uint32_t root_r = 1;
+  for (uint32_t t = 1; t < rcap; t++) {
+    const uint32_t* B = st.masks + (size_t)t * W;  // B_t
+    if (q >= 0) {
+      q = top_below<W>(nullptr, B, q);
+      if (q >= 0) root_r = t + 1;
+    }
+    bool any = false;
+    for (int w = 0; w < W; w++) {
+      const int i = (w << 5) + (int)lane;
+      bool has = false;
+      if (i < d) {
+        const int np = top_below<W>(st.rows + (size_t)i * W, B, (int)st.pidx[i]);
+        has = np >= 0;
+        st.pidx[i] = (uint16_t)(has ? np : 0);  // 0: no further round can succeed
+        if (has) st.rr[i] = (uint8_t)(t + 1);
+      }
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, has);
+      if (lane == 0 && t + 1 < rcap) st.masks[(size_t)(t + 1) * W + w] = bal;
+      any |= bal != 0u;
+    }
+    __syncwarp();
+    if (!any && q < 0) break;
+  }
+  __syncwarp();
+  return root_r;
+}
+
 // Steps 1 and 2 for root u: bitmap rows, Algorithm 5, masks.  Returns false
 // when the soft-embedding test drops the root.
 template <int W>
@@ -562,28 +632,7 @@ __device__ bool build_root(WarpState<W>& st, const EnumKArgs& a, uint32_t u, int
   // Algorithm 5 on G[N(u) ∪ {u}], r capped at k
   const uint32_t rcap = k;
   if (a.prune) {
-    uint32_t root_r = rcap;
-    if (lane == 0) {
-      for (int i = d - 1; i >= 0; i--) {
-        uint32_t c = 1;
-        const uint32_t* row = st.rows + (size_t)i * W;
-        for (int w = W - 1; w >= 0 && c < rcap; w--) {
-          uint32_t x = row[w];
-          while (x && c < rcap) {
-            int b = 31 - __clz(x);
-            x &= ~(1u << b);
-            if (c <= st.rr[(w << 5) + b]) c++;
-          }
-        }
-        st.rr[i] = (uint8_t)c;
-      }
-      uint32_t c = 1;
-      for (int j = d - 1; j >= 0 && c < rcap; j--)
-        if (c <= st.rr[j]) c++;
-      root_r = c;
-    }
-    root_r = __shfl_sync(0xFFFFFFFFu, root_r, 0);
-    __syncwarp();
+    const uint32_t root_r = soft_embedding<W>(st, d, rcap);
     if (root_r < k) {
       if (lane == 0) st.stats[kWsPruned]++;
       return false;

@@ -69,6 +69,7 @@ class kc_opts(ctypes.Structure):
         ("autotune", ctypes.c_uint32),
         ("tune_cache", ctypes.c_char_p),
         ("no_plex", ctypes.c_uint32),
+        ("memo_min_k", ctypes.c_uint32),
     ]
 
 
@@ -252,10 +253,10 @@ def kc_strerror(status: int) -> str:
 
 def kc_create(device: int = 0, no_memo: bool = False, no_prune: bool = False, memo_bytes: int = 0,
               spin_limit: int = 0, split_threshold: int = 0, decomposition: int = 0, autotune: bool = False,
-              tune_cache: str | None = None, no_plex: bool = False) -> int:
+              tune_cache: str | None = None, no_plex: bool = False, memo_min_k: int = 0) -> int:
     o = kc_opts(ctypes.sizeof(kc_opts), int(no_memo), int(no_prune), int(split_threshold), int(memo_bytes),
                 int(spin_limit), int(decomposition), int(autotune), tune_cache.encode() if tune_cache else None,
-                int(no_plex))
+                int(no_plex), int(memo_min_k))
     h = ctypes.c_void_p()
     _check(load().kc_create(ctypes.byref(h), int(device), ctypes.byref(o)), "kc_create")
     return h.value

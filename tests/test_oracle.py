@@ -414,6 +414,57 @@ def test_alg5_plants_a_mistake():
     assert any(r[u] != (n - 1 - u) + 1 for u in order)
 
 
+def _alg5_by_rounds(order, out, rcap):
+    """Algorithm 5 in the round form the device uses: B_1 is every vertex;
+    round t moves each vertex's increment point p to the largest out-neighbour
+    in B_t below p, and the vertices that found one form B_{t+1}.  Returns r
+    capped at rcap, and the capped r of a root adjacent to every vertex."""
+    pos = {v: i for i, v in enumerate(order)}
+    p = {u: len(order) for u in order}
+    r = {u: 1 for u in order}
+    b = set(order)
+    q, root = len(order), 1
+    for t in range(1, rcap):
+        below = [pos[v] for v in b if pos[v] < q]
+        q = max(below) if below else -1
+        if q >= 0:
+            root = t + 1
+        nb = set()
+        for u in order:
+            c = [pos[w] for w in out[u] if w in b and pos[w] < p[u]]
+            p[u] = max(c) if c else 0
+            if c:
+                r[u] = t + 1
+                nb.add(u)
+        b = nb
+    return r, root
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_alg5_round_form_equals_vertex_order(seed):
+    """The device computes Algorithm 5 by rounds over the sets B_t of
+    vertices with r >= t (all rows at once) instead of vertex by vertex.  On
+    random DAGs, for every cap, the two give the same capped r values, and the
+    same r for a root adjacent to every vertex (the root's own test)."""
+    rng = np.random.default_rng(seed)
+    for _ in range(40):
+        n = int(rng.integers(1, 40))
+        dens = float(rng.random())
+        order = [int(x) for x in rng.permutation(n)]
+        out = {u: set() for u in order}
+        for i in range(n):
+            for j in range(i + 1, n):
+                if rng.random() < dens:
+                    out[order[i]].add(order[j])
+        r = oracle.soft_embedding_r(order, out)
+        apex = max(order) + 1  # a root before every vertex, adjacent to all
+        r_root = oracle.soft_embedding_r([apex] + order, {**out, apex: set(order)})[apex]
+        for rcap in (2, 3, 5, 9, 64):
+            got, root = _alg5_by_rounds(order, out, rcap)
+            assert got == {u: min(r[u], rcap) for u in order}
+            assert root == min(r_root, rcap)
+
+
 # -------------------------------------------------------- input determinism
 def test_generator_fingerprints():
     """The seeded generators give the same bytes on every host."""

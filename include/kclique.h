@@ -169,9 +169,10 @@ int kc_export_dag(kc_ctx* ctx, kc_graph g, uint32_t* core, uint32_t* rank, uint6
  * Count the k-cliques of an uploaded graph (Definition 1) into *count (host).
  * k = 1 gives n, k = 2 gives m.  Work per root u of the DAG: the (k-1)-cliques
  * of the subgraph induced by N(u) (Algorithm 2), pruned by soft embeddings
- * (Sec. V) and, for dense subgraphs by Eq. (1), reusing repeated sub-counts
- * through a device form of the Induced Subgraph Trie (Sec. IV, Algorithms
- * 3-4).  Synchronises the stream.
+ * (Sec. V), with candidate sets that are 2-plexes counted in closed form
+ * (Sec. VII-A) and, for dense subgraphs by Eq. (1) and k >= memo_min_k,
+ * repeated sub-counts reused through a device form of the Induced Subgraph
+ * Trie (Sec. IV, Algorithms 3-4).  Synchronises the stream.
  */
 int kc_count(kc_ctx* ctx, kc_graph g, uint32_t k, uint64_t* count, void* stream);
 

@@ -278,8 +278,7 @@ static int enum_common(kc_ctx* ctx, kc_graph h, uint32_t k, int mode, uint32_t l
   ea.root_hi = hi;
   ea.d_buf = d_buf;
   ea.cap = d_buf ? cap : 0;
-  const uint32_t memo_min = ctx->opts.memo_min_k ? ctx->opts.memo_min_k : (ctx->opts.no_plex ? 3u : 8u);
-  ea.memo = ctx->opts.no_memo == 0 && (mode == 1 || k >= memo_min);
+  ea.memo = mode == 1 ? ctx->opts.no_memo == 0 : count_uses_memo(ctx, k);
   ea.prune = ctx->opts.no_prune == 0;
   KC_TRY(run_enum(ctx, g, ea, s));
   uint64_t tot = ctx->h_acc[kAccCount];

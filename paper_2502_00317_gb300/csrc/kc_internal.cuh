@@ -196,6 +196,13 @@ enum ScratchSlot : int {
   kScrSlots
 };
 
+// Whether a single-graph count of k-cliques uses the memo (kc_opts.memo_min_k;
+// default from k = 8 with the 2-plex closed form on, from k = 3 with it off).
+inline bool count_uses_memo(const kc_ctx* ctx, uint32_t k) {
+  const uint32_t min_k = ctx->opts.memo_min_k ? ctx->opts.memo_min_k : (ctx->opts.no_plex ? 3u : 8u);
+  return ctx->opts.no_memo == 0 && k >= min_k;
+}
+
 int scratch_get(kc_ctx* ctx, int slot, size_t bytes, void** out);
 int cuda_fail(kc_ctx* ctx, cudaError_t e, const char* what);
 

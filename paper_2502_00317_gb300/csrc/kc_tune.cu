@@ -63,7 +63,7 @@ int run_probe(kc_ctx* ctx, const ProbeWork& w, cudaStream_t s) {
     ea.mode = 0;
     ea.root_lo = w.lo;
     ea.root_hi = w.hi;
-    ea.memo = ctx->opts.no_memo == 0;
+    ea.memo = count_uses_memo(ctx, w.k);  // as kc_count would run it
     ea.prune = ctx->opts.no_prune == 0;
     return run_enum(ctx, *w.g, ea, s);
   }

@@ -23,6 +23,12 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    # the same workload description as the GPU arm's line (the same k sweep on the same graph)
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert d["config"] == bench._config("chung_lu_n1e5_planted200_seed1", bench.KS, 1)
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
 
 
 def test_build_algorithmic_bytes_by_definition():

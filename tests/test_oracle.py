@@ -127,6 +127,49 @@ def test_complete_minus_matching_closed_form(n, p):
         assert og.count(k)[0] == want, (n, p, k)
 
 
+def _plex2_test(S, adj):
+    """The device's 2-plex test on a vertex set S (ascending): p = non-edges;
+    reject when 2p > |S|; each vertex v may miss at most one vertex above it
+    (M_v); the vertices with a missing one and the missing ones together must
+    number 2p (all endpoints distinct)."""
+    m = len(S)
+    e = sum(1 for i in range(m) for j in range(i + 1, m) if S[j] in adj[S[i]])
+    p = m * (m - 1) // 2 - e
+    if 2 * p > m:
+        return False
+    touched = set()
+    for i, v in enumerate(S):
+        miss = [w for w in S[i + 1:] if w not in adj[v]]
+        if len(miss) > 1:
+            return False
+        if miss:
+            touched.add(v)
+            touched.add(miss[0])
+    return len(touched) == 2 * p
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_plex2_test_accepts_exactly_matchings(seed):
+    """The device counts a candidate set in closed form when its test accepts
+    it; the test accepts exactly the sets whose non-edges form a matching
+    (every vertex misses at most one other: a 2-plex), checked against that
+    definition on near-complete random graphs and all their small subsets."""
+    rng = np.random.default_rng(seed)
+    n = 9
+    for _ in range(30):
+        miss = float(rng.choice([0.05, 0.15, 0.3]))
+        adj = {v: set() for v in range(n)}
+        for a in range(n):
+            for b in range(a + 1, n):
+                if rng.random() >= miss:
+                    adj[a].add(b)
+                    adj[b].add(a)
+        for m in range(2, n + 1):
+            for S in itertools.combinations(range(n), m):
+                deg_miss = [sum(1 for w in S if w != v and w not in adj[v]) for v in S]
+                assert _plex2_test(list(S), adj) == (max(deg_miss) <= 1), (S, deg_miss)
+
+
 # ------------------------------------------------------------ brute force
 @pytest.mark.parametrize("seed", range(12))
 def test_random_tiny_graphs_brute_force(seed):
